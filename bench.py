@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the unfolding path: station.direction unfolds per second.
+
+Workload (one step): the 124-station direction scan -- 124 stations x 2 channels x 2048
+float32 samples at 200 MHz, 64 candidate directions (zenith 0-60 deg x 8, azimuth 0-315 deg
+x 8), the 19 x 72 x 51 synthetic VEL table -- unfolded pair by pair through the C ABI
+(ar_unfold: station transform, fused unfold, residual). 7936 pairs per step.
+
+  value        pairs / s over the K timed steps (device time, CUDA events per step on the
+               launching stream, L2 flushed by a 256 MiB write between steps, outside the
+               step's events), summed over ranks; max over ranks of the time
+  e2e          the same metric through ar_unfold_host with pinned host buffers: the inputs'
+               host->device copy, the kernels, and the device->host copy of every output
+               inside each timed step (host wall clock)
+  roofline     the fused unfold kernel: algorithmic bytes per launch / its mean duration
+               (CUDA events recorded by the library around it, same stream) vs measured HBM
+  cpu_baseline the FP64 oracle on a bounded sample of the same workload on the host cores
+
+--impl reference times the oracle alone (each step: one station x 16 directions of the
+same workload) and prints the same JSON line with "impl": "reference".
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload ("replicas only":
+the pairs are independent and need no exchange); value is all ranks' pairs over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "station-direction unfolds/s (124 st x 2048 samples x 64 dirs, FP32, <=1e-5 rel err)"
+UNIT = "unfolds/s"
+WORKLOAD = "direction scan: 124 stations x 2 ch x 2048 float32 @ 200 MHz, 64 directions (8 zen 0-60 x 8 az 0-315), 19x72x51 VEL table"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "unfold_kernel_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "dft.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1507_07733_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---- distributed plumbing ---------------------------------------------------------------
+
+def dist_setup(want_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if want_cuda else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks -----------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampled every 20 ms in the background; samples keep their host timestamps."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)   # let the first samples arrive
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.05)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = []
+        for ts, line in self.samples:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((ts, float(p[1]), float(p[2]), p[4], p[5:9]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        window = "timed region"
+        if len(inside) < 3 and rows:   # a short timed region: take the samples nearest to it
+            rows.sort(key=lambda r: 0 if t0 <= r[0] <= t1 else min(abs(r[0] - t0), abs(r[0] - t1)))
+            inside = rows[:3]
+            window = "timed region plus nearest samples"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in inside for n, v in zip(names, r[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "window": window}
+
+
+# ---- algorithmic work -----------------------------------------------------------------
+
+def unfold_bytes_per_launch(S: int, D: int, N: int, n_f: int) -> int:
+    """Bytes the fused unfold kernel must move: writes of E-field (8N), envelope (4N), peak
+    index/amplitude/time/status (20 B) per pair; reads of each station's band spectrum
+    (N/4 bins x 16 B) and each direction's four corner slabs (4 x n_f x 32 B) once."""
+    return S * D * (12 * N + 20) + S * (N // 4) * 16 + D * 4 * n_f * 32
+
+
+def unfold_flops_per_pair(N: int, D: int) -> float:
+    """benchFFT convention: two complex N-point inverse transforms (5 N log2 N each), ~16 N for
+    solve, envelope and peak, plus the station's forward transform amortised over D."""
+    import math
+    return 10 * N * math.log2(N) + 16 * N + 5 * N * math.log2(N) / D
+
+
+# ---- CPU (oracle) sample -------------------------------------------------------------------
+
+def oracle_sample(pat, ev, n_dirs: int = 16, station: int = 0):
+    from paper_1507_07733_gb300 import synth
+    return synth.Event(ev.traces[station:station + 1], ev.pos_m[station:station + 1],
+                       ev.t_start_ns[station:station + 1], ev.dirs_rad[:n_dirs], ev.fs_hz)
+
+
+def time_oracle(pat, ev, steps: int, warmup: int):
+    import oracle
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count() or 1
+    oracle.set_threads(threads)
+    pairs = 0
+    dt = 0.0
+    for k in range(warmup + steps):
+        sub = oracle_sample(pat, ev, 16, station=k % ev.n_stations)
+        t = time.perf_counter()
+        oracle.unfold_event(pat, sub)
+        el = time.perf_counter() - t
+        if k >= warmup:
+            dt += el
+            pairs += sub.n_stations * sub.n_dirs
+    return pairs, dt, threads
+
+
+# ---- the GPU arm -----------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1507_07733_gb300 import binding, synth
+
+    pat = synth.make_pattern()
+    ev = synth.direction_scan()
+    S, N, D = ev.n_stations, ev.n_samples, ev.n_dirs
+    ctx = binding.Context(local)
+    pid = ctx.load_pattern(pat)
+    ctx.prepare(N, ev.fs_hz, pid, S)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    tr, pos, ts, dirs = t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad)
+    out, ost = binding.alloc_outputs(D, S, N, device=dev)
+    evs = binding.make_event(pid, tr, pos, ts, dirs, ev.fs_hz, 1.0)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        binding.ar_unfold(ctx.h, evs, ost, sp)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    binding.ar_sync(ctx.h, sp)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    h0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    h1 = time.perf_counter()
+    clocks.stop()
+    binding.ar_sync(ctx.h, sp)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = allmax(world, sum(step_ms), dev)
+    pairs = S * D
+    value = pairs * world * args.steps / (total_ms / 1e3)
+
+    # the fused kernel's own duration, from events the library records around it
+    binding.ar_set_profiling(ctx.h, True)
+    k_ms = []
+    for _ in range(min(args.steps, 200)):
+        flush.zero_()
+        step()
+        k_ms.append(binding.ar_kernel_times(ctx.h))
+    binding.ar_set_profiling(ctx.h, False)
+    binding.ar_sync(ctx.h, sp)
+    k3 = statistics.mean(m[1] for m in k_ms)
+    k1 = statistics.mean(m[0] for m in k_ms)
+    k4 = statistics.mean(m[2] for m in k_ms)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    nbytes = unfold_bytes_per_launch(S, D, N, pat.n_freq)
+    achieved = nbytes / (k3 / 1e3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        pt = json.load(open(PROFILE_TRAFFIC))
+        if pt.get("kernel_hash") == kernel_source_hash():
+            traffic = pt.get("dram_bytes_per_launch")
+    sm_clock = 2070e6
+    fp32_peak = 152 * 128 * 2 * sm_clock / 1e12   # TFLOP/s, FFMA on every FP32 lane at max clock
+    flops = unfold_flops_per_pair(N, D) * pairs
+    alu = {"bound": "alu", "achieved": round(flops / (k3 / 1e3) / 1e12, 2), "peak": round(fp32_peak, 1),
+           "unit": "TFLOP/s", "frac": round(flops / (k3 / 1e3) / 1e12 / fp32_peak, 3),
+           "flops_per_launch": flops, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+
+    # end to end through the host-buffer entry point (pinned host memory both ways)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        htr, hpos, hts, hdirs = pin(ev.traces), pin(ev.pos_m), pin(ev.t_start_ns), pin(ev.dirs_rad)
+        hout, host = binding.alloc_outputs(D, S, N, device="cpu", pin_memory=True)
+        hev = binding.make_event(pid, htr, hpos, hts, hdirs, ev.fs_hz, 1.0)
+        n_e2e = max(3, min(args.steps, 50))
+        for _ in range(2):
+            binding.ar_unfold_host(ctx.h, hev, host, sp)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            binding.ar_unfold_host(ctx.h, hev, host, sp)
+        el = allmax(world, time.perf_counter() - t0, dev)
+        h2d = sum(x.numel() * x.element_size() for x in (htr, hpos, hts, hdirs))
+        d2h = sum(v.numel() * v.element_size() for v in hout.values() if v is not None)
+        e2e = {"value": round(pairs * world * n_e2e / el, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": round(el / n_e2e * 1e3, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        p_pairs, p_dt, threads = time_oracle(pat, ev, steps=args.cpu_steps, warmup=1)
+        cpu = {"value": round(p_pairs / p_dt, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_steps} x (1 station x 16 directions) of the workload, FP64 oracle "
+                         f"(naive DFTs), OpenMP over pairs; {p_pairs} pairs in {p_dt:.2f} s"}
+
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "stations": S, "samples": N, "directions": D,
+                       "pairs_per_step": pairs, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MiB write, outside the step events)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 3), "traffic": traffic, "peak_source": peak_src,
+                         "kernel": "unfold_kernel<2048>", "kernel_ms": round(k3, 5),
+                         "algorithmic_bytes_per_launch": nbytes},
+            "roofline_alu": alu,
+            "kernel_ms": {"station_spectrum": round(k1, 5), "unfold": round(k3, 5), "residual": round(k4, 5)},
+            "gpu_launches": 3 * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(h0, h1),
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---- the reference arm (the oracle, on the host cores) ---------------------------------
+
+def run_reference(args):
+    world, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    from paper_1507_07733_gb300 import synth
+    pat = synth.make_pattern()
+    ev = synth.direction_scan()
+    pairs, dt, threads = time_oracle(pat, ev, steps=args.steps, warmup=args.warmup)
+    value = pairs / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "stations": ev.n_stations, "samples": ev.n_samples,
+                   "directions": ev.n_dirs, "sample_per_step": "1 station x 16 directions"},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps x (1 station x 16 directions), FP64 oracle, "
+                                   f"OpenMP over pairs"},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--cpu-steps", type=int, default=40, help="oracle sample steps for cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * aerafold.h -- C ABI of the AERA antenna-response unfolding library (GB300, sm_103a).
+ *
+ * The library evaluates, for every (station, candidate arrival direction) pair of a radio
+ * event, the reconstruction step of arXiv 1507.07733, Sec. 2: the two-channel voltage
+ * traces are taken to the frequency domain, the antenna vector effective length (VEL) is
+ * interpolated for the direction from a tabulated (zenith, azimuth, frequency) pattern
+ * (Sec. 3), a 2x2 complex system is solved per frequency bin for the E-field components
+ * (E_theta, E_phi), the field is transformed back with its Hilbert envelope (Sec. 4), the
+ * envelope maximum gives the station timing, and per direction the timing is compared with
+ * a plane wave (the quantity the paper's triangulation minimises, Sec. 2).
+ *
+ * Conventions (fixed by this library where the paper is silent):
+ *  - Forward DFT  X[k] = sum_n x[n] exp(-2 pi i k n / N), unnormalised.
+ *  - The band is 30 MHz <= k fs / N <= 80 MHz (Sec. 1), both edges inclusive; every other
+ *    bin of the unfolded field is zero. fs must make the band at most N/4 bins wide and
+ *    keep 80 MHz below fs/2 (fs = 200 MHz gives exactly N/4 bins).
+ *  - VEL interpolation is trilinear in (zenith, azimuth, frequency), real and imaginary
+ *    parts separately; zenith and frequency clamp to the table, azimuth is periodic.
+ *  - Solve: det = H0t H1p - H0p H1t, E_t = (H1p V0 - H0p V1)/det, E_p = (H0t V1 - H1t V0)/det
+ *    where H[c][p] is the VEL of channel c for polarisation p. A bin with
+ *    |det| <= 1e-6 (|H0t||H1p| + |H0p||H1t|) is near-singular: E = 0 there and the pair's
+ *    status gets AR_STATUS_SINGULAR.
+ *  - Analytic signal z_p[n] = (1/N) sum_{k in band} 2 E_p[k] exp(+2 pi i k n / N);
+ *    E-field e_p = Re z_p; envelope env = sqrt(|z_theta|^2 + |z_phi|^2) (Sec. 4, read as the
+ *    modulus of the analytic signal of each component, summed in quadrature).
+ *  - Peak = argmax_n env[n], lowest index on exact ties; peak time = t_start + peak*1e9/fs ns.
+ *  - Direction (zenith, azimuth) in radians, azimuth counter-clockwise from east (+x);
+ *    n = (sin zen cos az, sin zen sin az, cos zen) points to the source. Plane-wave delay
+ *    tau_s = -n.x_s * n_refr / c; t0 = mean_s(t_s - tau_s); residual r_s = t_s - tau_s - t0;
+ *    chi2 = sum_s r_s^2. Positions in metres, times in ns, c = 299792458 m/s.
+ *
+ * Arithmetic: transforms, interpolation and solve in FP32; direction -> grid coordinates and
+ * all timing (peak time, residual, t0, chi2) in FP64.
+ *
+ * Threading: one ar_ctx may be used from one host thread at a time. Calls taking a stream
+ * are asynchronous on it unless stated otherwise. No call throws; every call returns an
+ * ar_status, and ar_last_error() gives the message of the last failure on that context.
+ */
+#ifndef AERAFOLD_H
+#define AERAFOLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ar_status {
+  AR_OK = 0,
+  AR_ERR_INVALID_ARG = 1,    /* a NULL pointer, a count out of range, a bad descriptor      */
+  AR_ERR_UNSUPPORTED_N = 2,  /* samples per channel not 1024, 2048 or 4096                 */
+  AR_ERR_NO_PATTERN = 3,     /* pattern id never returned by ar_load_pattern              */
+  AR_ERR_OUT_OF_MEMORY = 4,  /* a device or pinned-host allocation failed                 */
+  AR_ERR_BUDGET = 5,         /* serving: the event does not fit the state budget at all   */
+  AR_ERR_CUDA = 6,           /* a CUDA runtime call failed (message names it)              */
+  AR_ERR_TIMEOUT = 7,        /* serving: ar_wait timed out                                  */
+  AR_ERR_NOT_READY = 8,      /* serving: ticket still in flight                             */
+  AR_ERR_DEVICE = 9          /* a kernel reported an internal error (a bounded wait ran out) */
+} ar_status;
+
+/* per-pair status bits (ar_outputs.status) */
+#define AR_STATUS_SINGULAR 1u    /* at least one in-band bin was near-singular (E set to 0) */
+#define AR_STATUS_ZEN_CLAMP 2u   /* the zenith lay outside the table and was clamped        */
+#define AR_STATUS_BAD_DIR 4u     /* the direction was not finite: every output of the pair is 0 */
+
+typedef struct ar_ctx ar_ctx;
+
+typedef struct ar_config {
+  int32_t device;               /* CUDA device ordinal                                      */
+  int32_t autotune;             /* 1: the batched path times its tile choices on first use  */
+  uint64_t state_budget_bytes;  /* serving admission budget for event state; 0 = 4 GiB      */
+} ar_config;
+
+/* Axes of a VEL table. Node (i, j, l) sits at zenith zen0 + i dzen, azimuth az0 + j daz,
+ * frequency f0 + l df. Azimuth is periodic: n_az * daz must equal 2 pi. */
+typedef struct ar_pattern_desc {
+  int32_t n_zen;  double zen0_rad;  double dzen_rad;
+  int32_t n_az;   double az0_rad;   double daz_rad;
+  int32_t n_freq; double f0_hz;     double df_hz;
+} ar_pattern_desc;
+
+/* One event. In ar_unfold every array is DEVICE memory owned by the caller; in
+ * ar_unfold_host every array is HOST memory. */
+typedef struct ar_event {
+  int32_t n_stations;          /* S >= 1                                                   */
+  int32_t n_samples;           /* N: 1024, 2048 or 4096                                    */
+  int32_t n_dirs;              /* D >= 1                                                   */
+  int32_t pattern_id;          /* from ar_load_pattern; every station uses this pattern    */
+  double fs_hz;                /* sample rate                                              */
+  double refractive_index;     /* n_refr of the plane-wave model; 0 means 1.0              */
+  const float* traces;         /* [S][2][N] float32 voltages; 16-byte aligned              */
+  const double* pos_m;         /* [S][3] station positions, metres                         */
+  const double* t_start_ns;    /* [S] time of sample 0 of each station's trace, ns         */
+  const double* dirs_rad;      /* [D][2] (zenith, azimuth), radians                        */
+} ar_event;
+
+/* Outputs, owned by the caller (DEVICE memory for ar_unfold, HOST memory for
+ * ar_unfold_host). efield and envelope may be NULL ("peaks only"); the others are required. */
+typedef struct ar_outputs {
+  float* efield;               /* [D][S][2][N]  e_theta, e_phi                             */
+  float* envelope;             /* [D][S][N]                                                */
+  int32_t* peak_idx;           /* [D][S]                                                   */
+  float* peak_amp;             /* [D][S] envelope at the peak                              */
+  double* peak_time_ns;        /* [D][S]                                                   */
+  double* residual_ns;         /* [D][S]                                                   */
+  double* t0_ns;               /* [D]                                                      */
+  double* chi2;                /* [D] ns^2                                                 */
+  uint32_t* status;            /* [D][S] AR_STATUS_* bits                                  */
+} ar_outputs;
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, defaults). The context owns
+ * the device copies of loaded patterns, per-length twiddle tables and a workspace arena.
+ * Errors: AR_ERR_INVALID_ARG (ctx NULL), AR_ERR_CUDA (no such device), AR_ERR_OUT_OF_MEMORY. */
+ar_status ar_create(ar_ctx** ctx, const ar_config* cfg);
+
+/* Synchronise the device, free everything the context owns, and free ctx. NULL is a no-op. */
+ar_status ar_destroy(ar_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none). Valid until the next call on ctx.
+ * ctx NULL gives the message of the last ar_create failure in this process. */
+const char* ar_last_error(const ar_ctx* ctx);
+
+/* Name of a status code. */
+const char* ar_status_string(ar_status s);
+
+/* Copy a VEL table to the device (Sec. 3: the patterns are copied and converted once and
+ * stay on the device; all antenna types fit at the same time). host_table is
+ * [n_zen][n_az][n_freq][2 channels][2 polarisations] complex64 (interleaved re, im), in
+ * host memory that the caller keeps. n_zen >= 2, n_az >= 2, 2 <= n_freq <= 256.
+ * Synchronous. Errors: AR_ERR_INVALID_ARG, AR_ERR_OUT_OF_MEMORY, AR_ERR_CUDA. */
+ar_status ar_load_pattern(ar_ctx* ctx, const ar_pattern_desc* desc, const float* host_table,
+                          int32_t* pattern_id);
+
+/* Prepare the per-length tables and the workspace for events of up to max_stations
+ * stations with n_samples samples at fs_hz using pattern_id, so that later ar_unfold calls
+ * of that shape allocate nothing (needed before capturing ar_unfold into a CUDA graph).
+ * Synchronous. Errors as ar_unfold's validation. */
+ar_status ar_prepare(ar_ctx* ctx, int32_t n_samples, double fs_hz, int32_t pattern_id,
+                     int32_t max_stations);
+
+/* Unfold every (station, direction) pair of ev into out, asynchronously on stream
+ * (a cudaStream_t; NULL = the legacy default stream). All pointers are device pointers.
+ * Three kernels run in order: the forward transform of each station's two channels, the
+ * fused per-pair interpolation + solve + inverse transform + envelope + peak, and the
+ * per-direction plane-wave residual. Validation errors are returned before any launch;
+ * a device-side error is reported by the next ar_sync on this context.
+ * If the shape was not prepared, the first call allocates (synchronously).
+ * Errors: AR_ERR_INVALID_ARG, AR_ERR_UNSUPPORTED_N, AR_ERR_NO_PATTERN,
+ * AR_ERR_OUT_OF_MEMORY, AR_ERR_CUDA. */
+ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream);
+
+/* Synchronise stream and report device-side errors raised since the last ar_sync
+ * (AR_ERR_DEVICE), then clear them. */
+ar_status ar_sync(ar_ctx* ctx, void* stream);
+
+/* ar_unfold on HOST buffers: copies the event's arrays to device memory owned by the
+ * context, runs the path on stream, copies every output back and synchronises. Returns
+ * when the outputs are in the caller's host arrays. Host arrays may be pageable; pinned
+ * memory makes the copies faster. Errors: as ar_unfold, plus AR_ERR_DEVICE. */
+ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream);
+
+/* Per-kernel timing. While enabled, ar_unfold records CUDA events on its stream around each
+ * of its three kernels. ar_kernel_times waits for the last ar_unfold's events and writes
+ * the durations in milliseconds: ms[0] station transform, ms[1] fused unfold, ms[2]
+ * residual. Errors: AR_ERR_INVALID_ARG (NULL, or no timed ar_unfold yet), AR_ERR_CUDA. */
+ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable);
+ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AERAFOLD_H */

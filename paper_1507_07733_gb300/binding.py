@@ -1,0 +1,269 @@
+"""Thin ctypes binding of ``libaerafold.so`` (the C ABI of include/aerafold.h).
+
+Argument marshalling only: every step of the unfolding runs in the library's CUDA kernels.
+Function names match the C ABI (``ar_create``, ``ar_load_pattern``, ``ar_unfold``, ...).
+``Context`` wraps them for PyTorch users: tensors supply device memory and streams, and
+are passed to the library as raw pointers.
+
+Loading fails loudly (``LibraryMissing``) when the library has not been built: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libaerafold.so")
+
+AR_OK = 0
+STATUS_NAMES = ["AR_OK", "AR_ERR_INVALID_ARG", "AR_ERR_UNSUPPORTED_N", "AR_ERR_NO_PATTERN",
+                "AR_ERR_OUT_OF_MEMORY", "AR_ERR_BUDGET", "AR_ERR_CUDA", "AR_ERR_TIMEOUT",
+                "AR_ERR_NOT_READY", "AR_ERR_DEVICE"]
+AR_STATUS_SINGULAR = 1
+AR_STATUS_ZEN_CLAMP = 2
+AR_STATUS_BAD_DIR = 4
+
+#: every symbol include/aerafold.h declares
+EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
+            "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times"]
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class ArError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class ar_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("state_budget_bytes", ctypes.c_uint64)]
+
+
+class ar_pattern_desc(ctypes.Structure):
+    _fields_ = [("n_zen", ctypes.c_int32), ("zen0_rad", ctypes.c_double), ("dzen_rad", ctypes.c_double),
+                ("n_az", ctypes.c_int32), ("az0_rad", ctypes.c_double), ("daz_rad", ctypes.c_double),
+                ("n_freq", ctypes.c_int32), ("f0_hz", ctypes.c_double), ("df_hz", ctypes.c_double)]
+
+
+class ar_event(ctypes.Structure):
+    _fields_ = [("n_stations", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("n_dirs", ctypes.c_int32),
+                ("pattern_id", ctypes.c_int32), ("fs_hz", ctypes.c_double),
+                ("refractive_index", ctypes.c_double), ("traces", ctypes.c_void_p),
+                ("pos_m", ctypes.c_void_p), ("t_start_ns", ctypes.c_void_p), ("dirs_rad", ctypes.c_void_p)]
+
+
+class ar_outputs(ctypes.Structure):
+    _fields_ = [("efield", ctypes.c_void_p), ("envelope", ctypes.c_void_p), ("peak_idx", ctypes.c_void_p),
+                ("peak_amp", ctypes.c_void_p), ("peak_time_ns", ctypes.c_void_p),
+                ("residual_ns", ctypes.c_void_p), ("t0_ns", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load the library once; raises ``LibraryMissing`` if it is not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise LibraryMissing(f"{p} not found: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(p)
+        vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        L.ar_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ar_config)]
+        L.ar_destroy.argtypes = [vp]
+        L.ar_last_error.argtypes = [vp]
+        L.ar_last_error.restype = ctypes.c_char_p
+        L.ar_status_string.argtypes = [ctypes.c_int]
+        L.ar_status_string.restype = ctypes.c_char_p
+        L.ar_load_pattern.argtypes = [vp, ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(i32)]
+        L.ar_prepare.argtypes = [vp, i32, dbl, i32, i32]
+        L.ar_unfold.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
+        L.ar_sync.argtypes = [vp, vp]
+        L.ar_unfold_host.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
+        L.ar_set_profiling.argtypes = [vp, i32]
+        L.ar_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        for name in EXPORTED:
+            if name not in ("ar_last_error", "ar_status_string"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+# ---- raw C-ABI wrappers (same names) ---------------------------------------------------
+
+def _check(ctx, st):
+    if st != AR_OK:
+        msg = load().ar_last_error(ctx).decode()
+        raise ArError(st, msg)
+
+
+def ar_create(device: int = 0, autotune: bool = False, state_budget_bytes: int = 0):
+    L = load()
+    h = ctypes.c_void_p()
+    cfg = ar_config(device, int(autotune), state_budget_bytes)
+    _check(None, L.ar_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return h
+
+
+def ar_destroy(ctx) -> None:
+    load().ar_destroy(ctx)
+
+
+def ar_last_error(ctx) -> str:
+    return load().ar_last_error(ctx).decode()
+
+
+def ar_status_string(st: int) -> str:
+    return load().ar_status_string(st).decode()
+
+
+def ar_load_pattern(ctx, pattern) -> int:
+    """``pattern`` has ``desc()`` (axes) and ``table`` ([nz][na][nf][2][2] complex64)."""
+    d = ar_pattern_desc(**pattern.desc())
+    tab = np.ascontiguousarray(pattern.table, dtype=np.complex64)
+    pid = ctypes.c_int32()
+    _check(ctx, load().ar_load_pattern(ctx, ctypes.byref(d), tab.ctypes.data, ctypes.byref(pid)))
+    return pid.value
+
+
+def ar_prepare(ctx, n_samples: int, fs_hz: float, pattern_id: int, max_stations: int) -> None:
+    _check(ctx, load().ar_prepare(ctx, n_samples, fs_hz, pattern_id, max_stations))
+
+
+def ar_unfold(ctx, ev: ar_event, out: ar_outputs, stream: int = 0) -> None:
+    _check(ctx, load().ar_unfold(ctx, ctypes.byref(ev), ctypes.byref(out), ctypes.c_void_p(stream)))
+
+
+def ar_sync(ctx, stream: int = 0) -> None:
+    _check(ctx, load().ar_sync(ctx, ctypes.c_void_p(stream)))
+
+
+def ar_unfold_host(ctx, ev: ar_event, out: ar_outputs, stream: int = 0) -> None:
+    _check(ctx, load().ar_unfold_host(ctx, ctypes.byref(ev), ctypes.byref(out), ctypes.c_void_p(stream)))
+
+
+def ar_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load().ar_set_profiling(ctx, int(enable)))
+
+
+def ar_kernel_times(ctx):
+    """(spectrum, unfold, residual) durations in ms of the last profiled ar_unfold."""
+    ms = (ctypes.c_float * 3)()
+    _check(ctx, load().ar_kernel_times(ctx, ms))
+    return tuple(ms)
+
+
+# ---- PyTorch-facing helpers ----------------------------------------------------------
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def make_event(pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
+               refractive_index: float = 1.0) -> ar_event:
+    """Build an ``ar_event`` from tensors (device or host, matching the call used)."""
+    S, two, N = traces.shape
+    assert two == 2
+    return ar_event(S, N, dirs_rad.shape[0], pattern_id, fs_hz, refractive_index,
+                    _ptr(traces), _ptr(pos_m), _ptr(t_start_ns), _ptr(dirs_rad))
+
+
+def alloc_outputs(n_dirs: int, n_stations: int, n_samples: int, device="cuda", traces: bool = True,
+                  pin_memory: bool = False):
+    """Allocate output tensors with the library's layouts; returns (dict, ar_outputs)."""
+    import torch
+    D, S, N = n_dirs, n_stations, n_samples
+    kw = dict(device=device)
+    if device == "cpu" and pin_memory:
+        kw["pin_memory"] = True
+    o = dict(
+        efield=torch.empty((D, S, 2, N), dtype=torch.float32, **kw) if traces else None,
+        envelope=torch.empty((D, S, N), dtype=torch.float32, **kw) if traces else None,
+        peak_idx=torch.empty((D, S), dtype=torch.int32, **kw),
+        peak_amp=torch.empty((D, S), dtype=torch.float32, **kw),
+        peak_time_ns=torch.empty((D, S), dtype=torch.float64, **kw),
+        residual_ns=torch.empty((D, S), dtype=torch.float64, **kw),
+        t0_ns=torch.empty((D,), dtype=torch.float64, **kw),
+        chi2=torch.empty((D,), dtype=torch.float64, **kw),
+        status=torch.empty((D, S), dtype=torch.int32, **kw),
+    )
+    return o, outputs_struct(o)
+
+
+def outputs_struct(o: dict) -> ar_outputs:
+    return ar_outputs(*[_ptr(o[k]) for k in ("efield", "envelope", "peak_idx", "peak_amp", "peak_time_ns",
+                                              "residual_ns", "t0_ns", "chi2", "status")])
+
+
+class Context:
+    """One library context on one device (PyTorch tensors in, tensors out)."""
+
+    def __init__(self, device: int = 0, autotune: bool = False, state_budget_bytes: int = 0):
+        self.device = device
+        self.h = ar_create(device, autotune, state_budget_bytes)
+
+    def close(self):
+        if self.h:
+            ar_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_pattern(self, pattern) -> int:
+        return ar_load_pattern(self.h, pattern)
+
+    def prepare(self, n_samples: int, fs_hz: float, pattern_id: int, max_stations: int) -> None:
+        ar_prepare(self.h, n_samples, fs_hz, pattern_id, max_stations)
+
+    def unfold(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
+               refractive_index: float = 1.0, out: dict | None = None, traces_out: bool = True,
+               stream=None, sync: bool = False) -> dict:
+        """Unfold an event held in device tensors; returns the output tensors (async unless sync)."""
+        import torch
+        S, _, N = traces.shape
+        D = dirs_rad.shape[0]
+        if out is None:
+            out, _ = alloc_outputs(D, S, N, device=traces.device, traces=traces_out)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        st = stream if stream is not None else torch.cuda.current_stream(traces.device)
+        ar_unfold(self.h, ev, outputs_struct(out), st.cuda_stream)
+        if sync:
+            ar_sync(self.h, st.cuda_stream)
+        return out
+
+    def sync(self, stream=None) -> None:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        ar_sync(self.h, st.cuda_stream)
+
+    def unfold_host(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
+                    refractive_index: float = 1.0, out: dict | None = None, traces_out: bool = True,
+                    stream=None) -> dict:
+        """ar_unfold_host: inputs and outputs are host (CPU) tensors; returns when done."""
+        import torch
+        S, _, N = traces.shape
+        D = dirs_rad.shape[0]
+        if out is None:
+            out, _ = alloc_outputs(D, S, N, device="cpu", traces=traces_out)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ar_unfold_host(self.h, ev, outputs_struct(out), st.cuda_stream)
+        return out

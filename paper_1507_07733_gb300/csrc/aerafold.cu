@@ -1,0 +1,550 @@
+// aerafold.cu -- host side of the C ABI in include/aerafold.h.
+//
+// The context owns: device copies of VEL tables (uploaded once, Sec. 3 of arXiv 1507.07733),
+// per-trace-length twiddle tables (computed once on the host in FP64), per-(length, rate,
+// pattern) frequency-cell tables, a workspace arena for the station spectra (the paper's
+// shared static device buffers of Sec. 4, kept resident here), and a device error word.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/aerafold.h"
+#include "kernels.cuh"
+
+using namespace aerafold;
+
+namespace {
+
+constexpr double kBandLoHz = 30e6;
+constexpr double kBandHiHz = 80e6;
+constexpr double kCMPerNs = 0.299792458;
+constexpr int kMaxFreqNodes = 256;
+
+struct PatternDev {
+  ar_pattern_desc desc;
+  float2* table = nullptr;
+  size_t bytes = 0;
+};
+
+struct LenTables {
+  float2* t1 = nullptr;    // [4][Q][P]
+  float2* twf = nullptr;   // [Q][P]
+  float2* wn = nullptr;    // [N]
+};
+
+struct KernelCfg {
+  size_t smem = 0;
+  int grid = 0;
+};
+
+std::mutex g_create_mu;
+std::string g_create_error;
+
+}  // namespace
+
+struct ar_ctx {
+  int device = 0;
+  int num_sms = 0;
+  ar_config cfg{};
+  std::string last_error;
+  std::vector<PatternDev> patterns;
+  std::map<std::pair<int, int>, LenTables> len_tables;                 // (N, k_lo)
+  std::map<std::tuple<int, double, int>, int2*> bin_tables;            // (N, fs, pattern)
+  std::map<std::pair<int, int>, KernelCfg> unfold_cfg;                 // (N, n_f)
+  float4* spec = nullptr;
+  size_t spec_bytes = 0;
+  unsigned* d_err = nullptr;
+  // device staging for ar_unfold_host
+  std::vector<std::pair<void*, size_t>> stage;   // slots, grown on demand
+  // per-kernel timing
+  bool profiling = false;
+  bool timed = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+ar_status fail(ar_ctx* ctx, ar_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->last_error = buf;
+  return st;
+}
+
+#define AR_CUDA(ctx, call)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? AR_ERR_OUT_OF_MEMORY : AR_ERR_CUDA, \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                           \
+    }                                                                                        \
+  } while (0)
+
+// first in-band bin and count; the band is [30, 80] MHz inclusive (same rule as the ABI doc)
+void band_window(int n, double fs, int* k_lo, int* count, int* k_hi) {
+  *k_lo = -1;
+  *count = 0;
+  *k_hi = -1;
+  for (int k = 0; k < n; ++k) {
+    const double f = static_cast<double>(k) * fs / static_cast<double>(n);
+    if (f >= kBandLoHz && f <= kBandHiHz) {
+      if (*k_lo < 0) *k_lo = k;
+      *k_hi = k;
+      ++*count;
+    }
+  }
+}
+
+float2 unit(long t, long n, int sign) {   // exp(sign * 2 pi i t / n), t reduced exactly
+  t %= n;
+  if (t < 0) t += n;
+  const double a = 2.0 * M_PI * static_cast<double>(t) / static_cast<double>(n);
+  return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(sign * std::sin(a)));
+}
+
+template <int N_>
+ar_status build_len_tables(ar_ctx* ctx, int k_lo, LenTables* lt) {
+  using L = Layout<N_>;
+  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P;
+  std::vector<float2> t1(4 * Q * P), twf(Q * P), wn(N);
+  for (int r = 0; r < 4; ++r)
+    for (int mb = 0; mb < Q; ++mb)
+      for (int ja = 0; ja < P; ++ja)
+        t1[(r * Q + mb) * P + ja] = unit(static_cast<long>(k_lo + ja) * (r + 4 * mb), N, +1);
+  for (int q = 0; q < Q; ++q)
+    for (int p = 0; p < P; ++p) twf[q * P + p] = unit(static_cast<long>(p) * q, M, -1);
+  for (int t = 0; t < N; ++t) wn[t] = unit(t, N, -1);
+  AR_CUDA(ctx, cudaMalloc(&lt->t1, t1.size() * sizeof(float2)));
+  AR_CUDA(ctx, cudaMalloc(&lt->twf, twf.size() * sizeof(float2)));
+  AR_CUDA(ctx, cudaMalloc(&lt->wn, wn.size() * sizeof(float2)));
+  AR_CUDA(ctx, cudaMemcpy(lt->t1, t1.data(), t1.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  AR_CUDA(ctx, cudaMemcpy(lt->twf, twf.data(), twf.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  AR_CUDA(ctx, cudaMemcpy(lt->wn, wn.data(), wn.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return AR_OK;
+}
+
+ar_status get_len_tables(ar_ctx* ctx, int n, int k_lo, LenTables** out) {
+  auto key = std::make_pair(n, k_lo);
+  auto it = ctx->len_tables.find(key);
+  if (it == ctx->len_tables.end()) {
+    LenTables lt;
+    ar_status st = n == 1024   ? build_len_tables<1024>(ctx, k_lo, &lt)
+                   : n == 2048 ? build_len_tables<2048>(ctx, k_lo, &lt)
+                               : build_len_tables<4096>(ctx, k_lo, &lt);
+    if (st != AR_OK) return st;
+    it = ctx->len_tables.emplace(key, lt).first;
+  }
+  *out = &it->second;
+  return AR_OK;
+}
+
+// per window bin: frequency cell of the pattern (or -1 outside the band) and its fraction
+ar_status get_bin_table(ar_ctx* ctx, int n, double fs, int pid, int k_lo, int2** out) {
+  auto key = std::make_tuple(n, fs, pid);
+  auto it = ctx->bin_tables.find(key);
+  if (it == ctx->bin_tables.end()) {
+    const ar_pattern_desc& pd = ctx->patterns[pid].desc;
+    const int m = n / 4;
+    std::vector<int2> bt(m);
+    for (int j = 0; j < m; ++j) {
+      const int k = k_lo + j;
+      const double f = static_cast<double>(k) * fs / static_cast<double>(n);
+      if (!(f >= kBandLoHz && f <= kBandHiHz)) {
+        bt[j] = make_int2(-1, 0);
+        continue;
+      }
+      double u = (f - pd.f0_hz) / pd.df_hz;
+      if (u < 0.0) u = 0.0;
+      if (u > static_cast<double>(pd.n_freq - 1)) u = static_cast<double>(pd.n_freq - 1);
+      int c = static_cast<int>(std::floor(u));
+      if (c > pd.n_freq - 2) c = pd.n_freq - 2;
+      const float t = static_cast<float>(u - static_cast<double>(c));
+      int tb;
+      std::memcpy(&tb, &t, sizeof tb);
+      bt[j] = make_int2(c, tb);
+    }
+    int2* d = nullptr;
+    AR_CUDA(ctx, cudaMalloc(&d, bt.size() * sizeof(int2)));
+    AR_CUDA(ctx, cudaMemcpy(d, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    it = ctx->bin_tables.emplace(key, d).first;
+  }
+  *out = it->second;
+  return AR_OK;
+}
+
+ar_status ensure_spec(ar_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->spec_bytes) return AR_OK;
+  if (ctx->spec) {
+    AR_CUDA(ctx, cudaDeviceSynchronize());
+    AR_CUDA(ctx, cudaFree(ctx->spec));
+    ctx->spec = nullptr;
+    ctx->spec_bytes = 0;
+  }
+  AR_CUDA(ctx, cudaMalloc(&ctx->spec, bytes));
+  ctx->spec_bytes = bytes;
+  return AR_OK;
+}
+
+template <int N_>
+ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
+  auto key = std::make_pair(N_, n_f);
+  auto it = ctx->unfold_cfg.find(key);
+  if (it == ctx->unfold_cfg.end()) {
+    KernelCfg kc;
+    kc.smem = UnfoldSmem<N_>::total(n_f);
+    AR_CUDA(ctx, cudaFuncSetAttribute(unfold_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kc.smem)));
+    int per_sm = 0;
+    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, Layout<N_>::T,
+                                                               kc.smem));
+    if (per_sm < 1) return fail(ctx, AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM (smem %zu)", N_, kc.smem);
+    kc.grid = per_sm * ctx->num_sms;
+    const size_t sp_smem = sizeof(float2) * (Layout<N_>::N + 4 * Layout<N_>::PLN);
+    AR_CUDA(ctx, cudaFuncSetAttribute(station_spectrum_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(sp_smem)));
+    it = ctx->unfold_cfg.emplace(key, kc).first;
+  }
+  *out = &it->second;
+  return AR_OK;
+}
+
+struct Resolved {
+  int k_lo = 0;
+  LenTables* lt = nullptr;
+  int2* binf = nullptr;
+  KernelCfg* kc = nullptr;
+};
+
+ar_status validate_shape(ar_ctx* ctx, int n, double fs, int pid, int* k_lo) {
+  if (n != 1024 && n != 2048 && n != 4096)
+    return fail(ctx, AR_ERR_UNSUPPORTED_N, "n_samples=%d: supported lengths are 1024, 2048, 4096", n);
+  if (!(fs > 0.0) || !std::isfinite(fs)) return fail(ctx, AR_ERR_INVALID_ARG, "fs_hz=%g must be positive", fs);
+  if (pid < 0 || pid >= static_cast<int>(ctx->patterns.size()))
+    return fail(ctx, AR_ERR_NO_PATTERN, "pattern_id=%d was not loaded", pid);
+  int lo, cnt, hi;
+  band_window(n, fs, &lo, &cnt, &hi);
+  if (cnt < 1) return fail(ctx, AR_ERR_INVALID_ARG, "no bin of N=%d at fs=%g Hz lies in 30-80 MHz", n, fs);
+  if (cnt > n / 4 || lo + n / 4 > n / 2 || 2 * hi >= n)
+    return fail(ctx, AR_ERR_INVALID_ARG,
+                "fs=%g Hz: the 30-80 MHz band (%d bins from %d) must fit N/4 bins below Nyquist", fs, cnt, lo);
+  *k_lo = lo;
+  return AR_OK;
+}
+
+ar_status resolve(ar_ctx* ctx, int n, double fs, int pid, int max_st, Resolved* rs) {
+  ar_status st = validate_shape(ctx, n, fs, pid, &rs->k_lo);
+  if (st != AR_OK) return st;
+  if ((st = get_len_tables(ctx, n, rs->k_lo, &rs->lt)) != AR_OK) return st;
+  if ((st = get_bin_table(ctx, n, fs, pid, rs->k_lo, &rs->binf)) != AR_OK) return st;
+  const int n_f = ctx->patterns[pid].desc.n_freq;
+  st = n == 1024 ? unfold_cfg<1024>(ctx, n_f, &rs->kc)
+       : n == 2048 ? unfold_cfg<2048>(ctx, n_f, &rs->kc)
+                   : unfold_cfg<4096>(ctx, n_f, &rs->kc);
+  if (st != AR_OK) return st;
+  return ensure_spec(ctx, sizeof(float4) * static_cast<size_t>(n / 4) * static_cast<size_t>(max_st));
+}
+
+template <int N_>
+ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, const Resolved& rs,
+                     cudaStream_t stream) {
+  using L = Layout<N_>;
+  const PatternDev& pat = ctx->patterns[ev->pattern_id];
+  SpectrumParams sp{ev->traces, ctx->spec, rs.lt->twf, rs.lt->wn, rs.k_lo};
+  const size_t sp_smem = sizeof(float2) * (L::N + 4 * L::PLN);
+  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[0], stream));
+  station_spectrum_kernel<N_><<<ev->n_stations, L::T, sp_smem, stream>>>(sp);
+  AR_CUDA(ctx, cudaGetLastError());
+  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[1], stream));
+
+  UnfoldParams up{};
+  up.spec = ctx->spec;
+  up.table = pat.table;
+  up.binf = rs.binf;
+  up.t1 = rs.lt->t1;
+  up.dirs = ev->dirs_rad;
+  up.t_start = ev->t_start_ns;
+  up.efield = out->efield;
+  up.envelope = out->envelope;
+  up.peak_idx = out->peak_idx;
+  up.peak_amp = out->peak_amp;
+  up.peak_time = out->peak_time_ns;
+  up.status = out->status;
+  up.err = ctx->d_err;
+  up.zen0 = pat.desc.zen0_rad;
+  up.dzen = pat.desc.dzen_rad;
+  up.az0 = pat.desc.az0_rad;
+  up.daz = pat.desc.daz_rad;
+  up.dt_ns = 1e9 / ev->fs_hz;
+  up.n_zen = pat.desc.n_zen;
+  up.n_az = pat.desc.n_az;
+  up.n_f = pat.desc.n_freq;
+  up.n_st = ev->n_stations;
+  up.n_dir = ev->n_dirs;
+  up.k_lo = rs.k_lo;
+  up.total_pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
+  const long long grid = std::min<long long>(rs.kc->grid, up.total_pairs);
+  unfold_kernel<N_><<<static_cast<int>(grid), L::T, rs.kc->smem, stream>>>(up);
+  AR_CUDA(ctx, cudaGetLastError());
+  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[2], stream));
+
+  ResidualParams rp{};
+  rp.pos = ev->pos_m;
+  rp.dirs = ev->dirs_rad;
+  rp.peak_time = out->peak_time_ns;
+  rp.residual = out->residual_ns;
+  rp.t0 = out->t0_ns;
+  rp.chi2 = out->chi2;
+  rp.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  rp.n_st = ev->n_stations;
+  rp.n_dir = ev->n_dirs;
+  residual_kernel<<<(ev->n_dirs + 3) / 4, 128, 0, stream>>>(rp);
+  AR_CUDA(ctx, cudaGetLastError());
+  if (ctx->profiling) {
+    AR_CUDA(ctx, cudaEventRecord(ctx->ev[3], stream));
+    ctx->timed = true;
+  }
+  return AR_OK;
+}
+
+ar_status check_event(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out) {
+  if (!ev || !out) return fail(ctx, AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+  if (ev->n_stations < 1 || ev->n_stations > (1 << 20))
+    return fail(ctx, AR_ERR_INVALID_ARG, "n_stations=%d out of [1, 2^20]", ev->n_stations);
+  if (ev->n_dirs < 1 || ev->n_dirs > (1 << 20))
+    return fail(ctx, AR_ERR_INVALID_ARG, "n_dirs=%d out of [1, 2^20]", ev->n_dirs);
+  if (!ev->traces || !ev->pos_m || !ev->t_start_ns || !ev->dirs_rad)
+    return fail(ctx, AR_ERR_INVALID_ARG, "event arrays must not be NULL");
+  if (reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0)
+    return fail(ctx, AR_ERR_INVALID_ARG, "traces must be 16-byte aligned");
+  if (!out->peak_idx || !out->peak_amp || !out->peak_time_ns || !out->residual_ns || !out->t0_ns || !out->chi2 ||
+      !out->status)
+    return fail(ctx, AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
+  if (!(ev->refractive_index >= 0.0) || !std::isfinite(ev->refractive_index))
+    return fail(ctx, AR_ERR_INVALID_ARG, "refractive_index must be finite and >= 0");
+  return AR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ar_status_string(ar_status s) {
+  switch (s) {
+    case AR_OK: return "AR_OK";
+    case AR_ERR_INVALID_ARG: return "AR_ERR_INVALID_ARG";
+    case AR_ERR_UNSUPPORTED_N: return "AR_ERR_UNSUPPORTED_N";
+    case AR_ERR_NO_PATTERN: return "AR_ERR_NO_PATTERN";
+    case AR_ERR_OUT_OF_MEMORY: return "AR_ERR_OUT_OF_MEMORY";
+    case AR_ERR_BUDGET: return "AR_ERR_BUDGET";
+    case AR_ERR_CUDA: return "AR_ERR_CUDA";
+    case AR_ERR_TIMEOUT: return "AR_ERR_TIMEOUT";
+    case AR_ERR_NOT_READY: return "AR_ERR_NOT_READY";
+    case AR_ERR_DEVICE: return "AR_ERR_DEVICE";
+  }
+  return "AR_ERR_UNKNOWN";
+}
+
+ar_status ar_create(ar_ctx** out, const ar_config* cfg) {
+  if (!out) return AR_ERR_INVALID_ARG;
+  *out = nullptr;
+  ar_config c{};
+  if (cfg) c = *cfg;
+  if (c.state_budget_bytes == 0) c.state_budget_bytes = 4ull << 30;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  auto create_fail = [&](ar_status st, const char* msg) {
+    std::lock_guard<std::mutex> lk(g_create_mu);
+    g_create_error = msg;
+    return st;
+  };
+  if (e != cudaSuccess) return create_fail(AR_ERR_CUDA, cudaGetErrorString(e));
+  if (c.device < 0 || c.device >= ndev) return create_fail(AR_ERR_CUDA, "no such CUDA device");
+  if ((e = cudaSetDevice(c.device)) != cudaSuccess) return create_fail(AR_ERR_CUDA, cudaGetErrorString(e));
+  ar_ctx* ctx = new ar_ctx;
+  ctx->device = c.device;
+  ctx->cfg = c;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
+      cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+    delete ctx;
+    return create_fail(AR_ERR_OUT_OF_MEMORY, "context allocation failed");
+  }
+  *out = ctx;
+  return AR_OK;
+}
+
+ar_status ar_destroy(ar_ctx* ctx) {
+  if (!ctx) return AR_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& p : ctx->patterns) cudaFree(p.table);
+  for (auto& kv : ctx->len_tables) {
+    cudaFree(kv.second.t1);
+    cudaFree(kv.second.twf);
+    cudaFree(kv.second.wn);
+  }
+  for (auto& kv : ctx->bin_tables) cudaFree(kv.second);
+  for (auto& s : ctx->stage) cudaFree(s.first);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(ctx->spec);
+  cudaFree(ctx->d_err);
+  delete ctx;
+  return AR_OK;
+}
+
+const char* ar_last_error(const ar_ctx* ctx) {
+  if (!ctx) {
+    std::lock_guard<std::mutex> lk(g_create_mu);
+    return g_create_error.c_str();
+  }
+  return ctx->last_error.c_str();
+}
+
+ar_status ar_load_pattern(ar_ctx* ctx, const ar_pattern_desc* d, const float* host_table, int32_t* pattern_id) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (!d || !host_table || !pattern_id) return fail(ctx, AR_ERR_INVALID_ARG, "NULL argument");
+  if (d->n_zen < 2 || d->n_az < 2 || d->n_freq < 2 || d->n_freq > kMaxFreqNodes)
+    return fail(ctx, AR_ERR_INVALID_ARG, "pattern sizes %d x %d x %d out of range", d->n_zen, d->n_az, d->n_freq);
+  if (!(d->dzen_rad > 0) || !(d->daz_rad > 0) || !(d->df_hz > 0) || !std::isfinite(d->zen0_rad) ||
+      !std::isfinite(d->az0_rad) || !std::isfinite(d->f0_hz))
+    return fail(ctx, AR_ERR_INVALID_ARG, "pattern axis steps must be positive and origins finite");
+  if (std::fabs(d->n_az * d->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
+    return fail(ctx, AR_ERR_INVALID_ARG, "azimuth axis must cover 2 pi (n_az * daz = %.17g)", d->n_az * d->daz_rad);
+  const size_t nodes = static_cast<size_t>(d->n_zen) * d->n_az * d->n_freq;
+  if (nodes * 4 > (1ull << 31)) return fail(ctx, AR_ERR_INVALID_ARG, "pattern too large");
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  PatternDev p;
+  p.desc = *d;
+  p.bytes = nodes * 4 * sizeof(float2);
+  AR_CUDA(ctx, cudaMalloc(&p.table, p.bytes));
+  cudaError_t e = cudaMemcpy(p.table, host_table, p.bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p.table);
+    return fail(ctx, AR_ERR_CUDA, "pattern upload failed: %s", cudaGetErrorString(e));
+  }
+  ctx->patterns.push_back(p);
+  *pattern_id = static_cast<int32_t>(ctx->patterns.size() - 1);
+  return AR_OK;
+}
+
+ar_status ar_prepare(ar_ctx* ctx, int32_t n_samples, double fs_hz, int32_t pattern_id, int32_t max_stations) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (max_stations < 1) return fail(ctx, AR_ERR_INVALID_ARG, "max_stations must be >= 1");
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  Resolved rs;
+  return resolve(ctx, n_samples, fs_hz, pattern_id, max_stations, &rs);
+}
+
+ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  ar_status st = check_event(ctx, ev, out);
+  if (st != AR_OK) return st;
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  Resolved rs;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (ev->n_samples) {
+    case 1024: return launch_all<1024>(ctx, ev, out, rs, s);
+    case 2048: return launch_all<2048>(ctx, ev, out, rs, s);
+    default: return launch_all<4096>(ctx, ev, out, rs, s);
+  }
+}
+
+ar_status ar_sync(ar_ctx* ctx, void* stream) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  AR_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned err = 0;
+  AR_CUDA(ctx, cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost));
+  if (err) {
+    AR_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+    return fail(ctx, AR_ERR_DEVICE, "device error 0x%x (a bounded wait for a bulk copy ran out)", err);
+  }
+  return AR_OK;
+}
+
+ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  ar_status st = check_event(ctx, ev, out);
+  if (st != AR_OK) return st;
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t S = ev->n_stations, D = ev->n_dirs, N = ev->n_samples;
+  if (N != 1024 && N != 2048 && N != 4096)
+    return fail(ctx, AR_ERR_UNSUPPORTED_N, "n_samples=%zu: supported lengths are 1024, 2048, 4096", N);
+  // staging slots: 0 traces, 1 pos, 2 t_start, 3 dirs, 4 efield, 5 envelope, 6 peak_idx,
+  // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status
+  const size_t sizes[13] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
+                            D * 2 * sizeof(double), out->efield ? D * S * 2 * N * sizeof(float) : 0,
+                            out->envelope ? D * S * N * sizeof(float) : 0, D * S * sizeof(int32_t),
+                            D * S * sizeof(float), D * S * sizeof(double), D * S * sizeof(double),
+                            D * sizeof(double), D * sizeof(double), D * S * sizeof(uint32_t)};
+  if (ctx->stage.size() < 13) ctx->stage.resize(13, {nullptr, 0});
+  for (int i = 0; i < 13; ++i) {
+    if (sizes[i] > ctx->stage[i].second) {
+      AR_CUDA(ctx, cudaDeviceSynchronize());
+      cudaFree(ctx->stage[i].first);
+      ctx->stage[i] = {nullptr, 0};
+      AR_CUDA(ctx, cudaMalloc(&ctx->stage[i].first, sizes[i]));
+      ctx->stage[i].second = sizes[i];
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto dev = [&](int i) { return ctx->stage[i].first; };
+  AR_CUDA(ctx, cudaMemcpyAsync(dev(0), ev->traces, sizes[0], cudaMemcpyHostToDevice, s));
+  AR_CUDA(ctx, cudaMemcpyAsync(dev(1), ev->pos_m, sizes[1], cudaMemcpyHostToDevice, s));
+  AR_CUDA(ctx, cudaMemcpyAsync(dev(2), ev->t_start_ns, sizes[2], cudaMemcpyHostToDevice, s));
+  AR_CUDA(ctx, cudaMemcpyAsync(dev(3), ev->dirs_rad, sizes[3], cudaMemcpyHostToDevice, s));
+  ar_event de = *ev;
+  de.traces = static_cast<const float*>(dev(0));
+  de.pos_m = static_cast<const double*>(dev(1));
+  de.t_start_ns = static_cast<const double*>(dev(2));
+  de.dirs_rad = static_cast<const double*>(dev(3));
+  ar_outputs dout{};
+  dout.efield = out->efield ? static_cast<float*>(dev(4)) : nullptr;
+  dout.envelope = out->envelope ? static_cast<float*>(dev(5)) : nullptr;
+  dout.peak_idx = static_cast<int32_t*>(dev(6));
+  dout.peak_amp = static_cast<float*>(dev(7));
+  dout.peak_time_ns = static_cast<double*>(dev(8));
+  dout.residual_ns = static_cast<double*>(dev(9));
+  dout.t0_ns = static_cast<double*>(dev(10));
+  dout.chi2 = static_cast<double*>(dev(11));
+  dout.status = static_cast<uint32_t*>(dev(12));
+  if ((st = ar_unfold(ctx, &de, &dout, stream)) != AR_OK) return st;
+  void* hosts[13] = {nullptr, nullptr, nullptr, nullptr, out->efield, out->envelope, out->peak_idx,
+                     out->peak_amp, out->peak_time_ns, out->residual_ns, out->t0_ns, out->chi2, out->status};
+  for (int i = 4; i < 13; ++i)
+    if (hosts[i] && sizes[i]) AR_CUDA(ctx, cudaMemcpyAsync(hosts[i], dev(i), sizes[i], cudaMemcpyDeviceToHost, s));
+  return ar_sync(ctx, stream);
+}
+
+ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (enable && !ctx->ev[0])
+    for (auto& e : ctx->ev) AR_CUDA(ctx, cudaEventCreate(&e));
+  ctx->profiling = enable != 0;
+  ctx->timed = false;
+  return AR_OK;
+}
+
+ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (!ms || !ctx->timed) return fail(ctx, AR_ERR_INVALID_ARG, "no timed ar_unfold to report");
+  AR_CUDA(ctx, cudaEventSynchronize(ctx->ev[3]));
+  for (int i = 0; i < 3; ++i) AR_CUDA(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+  return AR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,556 @@
+// kernels.cuh -- device side of the unfolding path (sm_103a).
+//
+//   station_spectrum_kernel  forward transform of each station's two channels, one complex
+//                            N-point DFT of (v0 + i v1) per station, split into the two real
+//                            channels' spectra; only the M = N/4 bins of the band window kept
+//   unfold_kernel            per (station, direction) pair: VEL interpolation (corner slabs of
+//                            the pattern staged by TMA bulk copies), 2x2 solve per bin, inverse
+//                            transform of the one-sided (analytic) spectrum, E-field, envelope,
+//                            peak; a persistent grid walks the pairs station-major
+//   residual_kernel          per direction, FP64 plane-wave timing residual, one warp each
+//
+// Transform layout. The band holds at most M = N/4 bins, k in [k_lo, k_lo + M). The inverse
+// transform z[n] = sum_k Z[k] exp(2 pi i k n / N) is evaluated at n = 4m + r (r = 0..3) as
+// four M-point transforms, each split as M = P * Q:
+//   j = k - k_lo = ja + P jb,  m = mb + Q ma
+//   z[4m + r] = sum_ja exp(2 pi i ((k_lo+ja) mod P) ma / P) *
+//               [ T1[r][mb][ja] * sum_jb (Z[k_lo+ja+P jb] exp(2 pi i jb r / 4Q)) exp(2 pi i jb mb / Q) ]
+//   T1[r][mb][ja] = exp(2 pi i (k_lo + ja)(r + 4 mb) / N)
+// Pass 1 is a Q-point DFT per (polarisation, r, ja); pass 2 a P-point DFT per (r, mb). The
+// output phase of the band offset is absorbed by rotating pass 2's input rows by k_lo mod P,
+// so no per-sample phase is applied at the end, and thread t of pass 2 writes samples
+// n = t + 4Q ma: every warp store is 128 contiguous bytes.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dft.cuh"
+
+namespace aerafold {
+
+constexpr unsigned kStSingular = 1u;
+constexpr unsigned kStZenClamp = 2u;
+constexpr unsigned kStBadDir = 4u;
+
+constexpr unsigned kErrTmaTimeout = 1u;     // a bounded mbarrier wait ran out
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+
+// ---- shapes per trace length ------------------------------------------------------------
+
+template <int N_>
+struct Shape;
+template <>
+struct Shape<1024> { static constexpr int N = 1024, M = 256, Q = 16, P = 16; };
+template <>
+struct Shape<2048> { static constexpr int N = 2048, M = 512, Q = 32, P = 16; };
+template <>
+struct Shape<4096> { static constexpr int N = 4096, M = 1024, Q = 32, P = 32; };
+
+template <int N_>
+struct Layout : Shape<N_> {
+  using S = Shape<N_>;
+  static constexpr int T = 8 * S::P;                  // threads: one pass-1 task each
+  static constexpr int SPLIT = T / (4 * S::Q);        // pass-2 threads per (r, mb): 1 or 2
+  static constexpr int LDA = S::Q + 1;                // row stride of A (float2)
+  static constexpr int PLN0 = S::P * LDA;
+  static constexpr int PLN = PLN0 + ((4 - PLN0 % 16) + 16) % 16;   // plane stride, == 4 mod 16
+  static constexpr int A_F2 = 8 * PLN;                // A: [pol][r][row][mb]; E aliases it
+  static constexpr int PW_F = SPLIT == 2 ? 2 * S::M : 0;   // |Y|^2 exchange between pol threads
+  static_assert(SPLIT == 1 || SPLIT == 2, "layout");
+  static_assert(A_F2 >= 2 * S::M, "E must fit in A");
+  static_assert(T % 32 == 0 && S::M % T == 0, "layout");
+};
+
+// ---- PTX helpers: shared-memory addresses, mbarrier, bulk copy, timer -------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase with the given parity to complete; false if it did not within limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+// 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---- K1: forward transform of the station voltages ---------------------------------------
+
+struct SpectrumParams {
+  const float* traces;     // [S][2][N]
+  float4* spec;            // [S][M]: (X0[k], X1[k]) for k = k_lo + j
+  const float2* twf;       // [Q][P]: exp(-2 pi i p q / M) at [q][p]
+  const float2* wn;        // [N]: exp(-2 pi i t / N)
+  int k_lo;
+};
+
+// Z[k] = sum_r W_N^{kr} U_r[k mod M], U_r = M-point DFT of x[4m + r]; the M-point DFT is
+// M = P * Q: input m = m1 + P m2, output k' = k2 + Q k1.
+template <int N_>
+__global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(SpectrumParams prm) {
+  using L = Layout<N_>;
+  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* xs = reinterpret_cast<float2*>(smem_raw);   // [4][M]: x[4m + r] at [r][m]; later U_r
+  float2* B = xs + N;                                   // [4][P][LDA] (plane stride PLN)
+  const int s = blockIdx.x;
+  const int tid = threadIdx.x;
+
+  const float4* v0 = reinterpret_cast<const float4*>(prm.traces + static_cast<size_t>(s) * 2 * N);
+  const float4* v1 = v0 + N / 4;
+  for (int m = tid; m < M; m += T) {
+    const float4 a = __ldg(v0 + m), b = __ldg(v1 + m);
+    xs[0 * M + m] = make_float2(a.x, b.x);
+    xs[1 * M + m] = make_float2(a.y, b.y);
+    xs[2 * M + m] = make_float2(a.z, b.z);
+    xs[3 * M + m] = make_float2(a.w, b.w);
+  }
+  __syncthreads();
+  // pass 1: task (r, m1), Q-point DFT over m2, twiddle W_M^{m1 k2}
+  for (int task = tid; task < 4 * P; task += T) {
+    const int r = task / P, m1 = task % P;
+    float2 x[Q];
+    static_for<0, Q>([&](auto m2) { x[m2] = xs[r * M + m1 + P * m2]; });
+    dft<Q, -1>(x);
+    static_for<0, Q>([&](auto k2) {
+      if constexpr (k2 != 0) x[k2] = cmul(x[k2], __ldg(prm.twf + k2 * P + m1));
+      B[r * PLN + m1 * LDA + k2] = x[k2];
+    });
+  }
+  __syncthreads();
+  // pass 2: task (r, k2), P-point DFT over m1 -> U_r[k2 + Q k1]
+  for (int task = tid; task < 4 * Q; task += T) {
+    const int r = task / Q, k2 = task % Q;
+    float2 y[P];
+    static_for<0, P>([&](auto m1) { y[m1] = B[r * PLN + m1 * LDA + k2]; });
+    dft<P, -1>(y);
+    static_for<0, P>([&](auto k1) { xs[r * M + k2 + Q * k1] = y[k1]; });
+  }
+  __syncthreads();
+  // combine the four decimated transforms at k and N - k, split the channels
+  float4* out = prm.spec + static_cast<size_t>(s) * M;
+  for (int j = tid; j < M; j += T) {
+    const int k = prm.k_lo + j;
+    const int kk = k % M, km = (M - kk) % M;
+    float2 z = xs[kk], zm = xs[km];
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+      const float2 w = __ldg(prm.wn + (k * r) % N);           // W_N^{kr}
+      z = cadd(z, cmul(xs[r * M + kk], w));
+      zm = cadd(zm, cmulc(xs[r * M + km], w));                // W_N^{-kr} = conj
+    }
+    const float2 sum = make_float2(z.x + zm.x, z.y - zm.y);   // Z[k] + conj Z[N-k]
+    const float2 dif = make_float2(z.x - zm.x, z.y + zm.y);   // Z[k] - conj Z[N-k]
+    out[j] = make_float4(0.5f * sum.x, 0.5f * sum.y, 0.5f * dif.y, -0.5f * dif.x);
+  }
+}
+
+// ---- K3: fused per-pair unfold ------------------------------------------------------------
+
+struct UnfoldParams {
+  const float4* spec;        // [S][M] station spectra in the band window
+  const float2* table;       // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
+  const int2* binf;          // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
+  const float2* t1;          // [4][Q][P] pass-1 output twiddles
+  const double* dirs;        // [D][2]
+  const double* t_start;     // [S]
+  float* efield;             // [D][S][2][N] or null
+  float* envelope;           // [D][S][N] or null
+  int* peak_idx;             // [D][S]
+  float* peak_amp;           // [D][S]
+  double* peak_time;         // [D][S]
+  unsigned* status;          // [D][S]
+  unsigned* err;             // device error word
+  double zen0, dzen, az0, daz, dt_ns;
+  int n_zen, n_az, n_f;
+  int n_st, n_dir, k_lo;
+  long long total_pairs;
+};
+
+struct DirInfo {
+  int slab0, slab1, slab2, slab3;   // node offsets (units of n_f * 4 float2) of the 4 corners
+  float w[4];                       // bilinear weights of the corners
+  unsigned st;
+  int pad;
+};
+
+// Direction -> pattern cell (FP64, no fused multiply-adds) -> FP32 bilinear weights.
+__device__ __forceinline__ DirInfo direction_cell(const UnfoldParams& p, double zen, double az) {
+  DirInfo di;
+  di.st = 0;
+  di.pad = 0;
+  if (!isfinite(zen) || !isfinite(az)) {
+    di.st = kStBadDir;
+    di.slab0 = di.slab1 = di.slab2 = di.slab3 = 0;
+    di.w[0] = di.w[1] = di.w[2] = di.w[3] = 0.f;
+    return di;
+  }
+  double uz = __ddiv_rn(__dsub_rn(zen, p.zen0), p.dzen);
+  if (uz < 0.0) { uz = 0.0; di.st |= kStZenClamp; }
+  if (uz > double(p.n_zen - 1)) { uz = double(p.n_zen - 1); di.st |= kStZenClamp; }
+  int iz = static_cast<int>(floor(uz));
+  if (iz > p.n_zen - 2) iz = p.n_zen - 2;
+  const double tz = __dsub_rn(uz, double(iz));
+  double ua = __ddiv_rn(__dsub_rn(az, p.az0), p.daz);
+  ua = __dsub_rn(ua, __dmul_rn(double(p.n_az), floor(__ddiv_rn(ua, double(p.n_az)))));
+  int ia = static_cast<int>(floor(ua));
+  const double ta = __dsub_rn(ua, double(ia));
+  if (ia >= p.n_az) ia -= p.n_az;
+  const int ia1 = ia + 1 == p.n_az ? 0 : ia + 1;
+  di.slab0 = iz * p.n_az + ia;          // (iz,   ia)
+  di.slab1 = (iz + 1) * p.n_az + ia;    // (iz+1, ia)
+  di.slab2 = iz * p.n_az + ia1;         // (iz,   ia+1)
+  di.slab3 = (iz + 1) * p.n_az + ia1;   // (iz+1, ia+1)
+  const double uz0 = __dsub_rn(1.0, tz), ua0 = __dsub_rn(1.0, ta);
+  di.w[0] = static_cast<float>(__dmul_rn(uz0, ua0));
+  di.w[1] = static_cast<float>(__dmul_rn(tz, ua0));
+  di.w[2] = static_cast<float>(__dmul_rn(uz0, ta));
+  di.w[3] = static_cast<float>(__dmul_rn(tz, ta));
+  return di;
+}
+
+// Pass 1 for one (pol, r, ja): load E_p[ja + P jb], pre-twiddle exp(2 pi i jb r / 4Q), Q-point
+// inverse DFT, output twiddle T1[r][mb][ja].
+template <int N_, int R>
+__device__ __forceinline__ void pass1_task(const float2* Ep, int ja, const float2* __restrict__ t1,
+                                           float2 (&x)[Layout<N_>::Q]) {
+  using L = Layout<N_>;
+  constexpr int Q = L::Q, P = L::P;
+  static_for<0, Q>([&](auto jb) {
+    x[jb] = twmul<long(decltype(jb)::value) * R, 4 * Q, +1>(Ep[ja + P * jb]);
+  });
+  dft<Q, +1>(x);
+  const float2* tw = t1 + (R * Q) * P + ja;
+  static_for<0, Q>([&](auto mb) { x[mb] = cmul(x[mb], __ldg(tw + mb * P)); });
+}
+
+template <int N_>
+struct UnfoldSmem {
+  using L = Layout<N_>;
+  // byte offsets inside dynamic shared memory (all 16-byte aligned)
+  static constexpr size_t A = 0;
+  static constexpr size_t PW = A + sizeof(float2) * L::A_F2;
+  static constexpr size_t SPEC = PW + ((sizeof(float) * L::PW_F + 15) / 16) * 16;
+  static constexpr size_t BINF = SPEC + sizeof(float4) * L::M;
+  static constexpr size_t DIR = BINF + sizeof(int2) * L::M;            // 2 DirInfo
+  static constexpr size_t RED = DIR + 2 * sizeof(DirInfo);             // T/32 (float,int) + flags
+  static constexpr size_t BAR = RED + 16 * (L::T / 32) + 16;
+  static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2
+  __host__ __device__ static size_t hn(int n_f) { return SLAB + sizeof(float2) * 16 * n_f; }
+  __host__ __device__ static size_t total(int n_f) { return hn(n_f) + sizeof(float2) * 4 * n_f; }
+};
+
+template <int N_>
+__global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm) {
+  using L = Layout<N_>;
+  using SM = UnfoldSmem<N_>;
+  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
+  constexpr int SPLIT = L::SPLIT;
+  constexpr int NB = M / T;   // solve bins per thread
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* A = reinterpret_cast<float2*>(smem_raw + SM::A);
+  float2* E = A;   // E[pol][j], consumed by pass 1 before A is written
+  float* PWX = reinterpret_cast<float*>(smem_raw + SM::PW);
+  float4* sspec = reinterpret_cast<float4*>(smem_raw + SM::SPEC);
+  int2* sbinf = reinterpret_cast<int2*>(smem_raw + SM::BINF);
+  DirInfo* sdir = reinterpret_cast<DirInfo*>(smem_raw + SM::DIR);
+  float* redv = reinterpret_cast<float*>(smem_raw + SM::RED);
+  int* redi = reinterpret_cast<int*>(redv + T / 32);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + SM::BAR);
+  float2* slab = reinterpret_cast<float2*>(smem_raw + SM::SLAB);
+  float2* hn = reinterpret_cast<float2*>(smem_raw + SM::hn(prm.n_f));
+
+  const int tid = threadIdx.x;
+  const int n_f = prm.n_f;
+  const unsigned slab_bytes = static_cast<unsigned>(n_f) * 4u * sizeof(float2);
+
+  // contiguous chunk of the station-major pair space
+  const long long per = prm.total_pairs / gridDim.x, rem = prm.total_pairs % gridDim.x;
+  const long long q0 = blockIdx.x * per + min(static_cast<long long>(blockIdx.x), rem);
+  const long long q1 = q0 + per + (blockIdx.x < rem ? 1 : 0);
+  if (q0 >= q1) return;
+
+  for (int j = tid; j < M; j += T) sbinf[j] = __ldg(prm.binf + j);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    const int d = static_cast<int>(q0 % prm.n_dir);
+    DirInfo di = direction_cell(prm, prm.dirs[2 * d], prm.dirs[2 * d + 1]);
+    sdir[0] = di;
+    mbar_arrive_expect_tx(bar, 4 * slab_bytes);
+    const float2* base = prm.table;
+    const size_t node = static_cast<size_t>(n_f) * 4;
+    tma_bulk_g2s(slab + 0 * n_f * 4, base + di.slab0 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 1 * n_f * 4, base + di.slab1 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 2 * n_f * 4, base + di.slab2 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 3 * n_f * 4, base + di.slab3 * node, slab_bytes, bar);
+  }
+  __syncthreads();   // barrier initialised, first direction and frequency cells visible
+  int cur_s = -1;
+  unsigned phase = 0;
+
+  for (long long q = q0; q < q1; ++q, phase ^= 1u) {
+    const int s = static_cast<int>(q / prm.n_dir), d = static_cast<int>(q % prm.n_dir);
+    const int buf = static_cast<int>((q - q0) & 1);
+    if (s != cur_s) {   // new station: its band-window spectrum into shared memory
+      const float4* src = prm.spec + static_cast<size_t>(s) * M;
+      for (int j = tid; j < M; j += T) sspec[j] = __ldg(src + j);
+      cur_s = s;
+    }
+    // corner slabs of this pair's direction
+    const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(prm.err, kErrTmaTimeout);
+      return;
+    }
+    const DirInfo di = sdir[buf];
+    // angular (bilinear) interpolation at every frequency node
+    for (int e = tid; e < n_f * 4; e += T) {
+      const float2 a = slab[e], b = slab[n_f * 4 + e], c = slab[2 * n_f * 4 + e], dd = slab[3 * n_f * 4 + e];
+      float2 h;
+      h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+      h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+      hn[e] = h;
+    }
+    __syncthreads();   // hn, sspec ready; slab free
+    if (tid == 0 && q + 1 < q1) {   // prefetch the next pair's slabs
+      const int dn = static_cast<int>((q + 1) % prm.n_dir);
+      DirInfo nx = direction_cell(prm, prm.dirs[2 * dn], prm.dirs[2 * dn + 1]);
+      sdir[buf ^ 1] = nx;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, 4 * slab_bytes);
+      const size_t node = static_cast<size_t>(n_f) * 4;
+      tma_bulk_g2s(slab + 0 * n_f * 4, prm.table + nx.slab0 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 1 * n_f * 4, prm.table + nx.slab1 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 2 * n_f * 4, prm.table + nx.slab2 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 3 * n_f * 4, prm.table + nx.slab3 * node, slab_bytes, bar);
+    }
+
+    // ---- frequency interpolation + 2x2 solve per bin ----
+    const bool valid = (di.st & kStBadDir) == 0;
+    bool sing = false;
+    constexpr float kScale = 2.0f / static_cast<float>(N);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int j = tid + T * i;
+      const int2 bf = sbinf[j];
+      float2 et = make_float2(0.f, 0.f), ep = et;
+      if (bf.x >= 0 && valid) {
+        const float tf = __int_as_float(bf.y);
+        const float4* h0 = reinterpret_cast<const float4*>(hn + 4 * bf.x);
+        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
+        const float2 a = make_float2(fmaf(tf, g01.x - h01.x, h01.x), fmaf(tf, g01.y - h01.y, h01.y));   // H0t
+        const float2 b = make_float2(fmaf(tf, g01.z - h01.z, h01.z), fmaf(tf, g01.w - h01.w, h01.w));   // H0p
+        const float2 c = make_float2(fmaf(tf, g23.x - h23.x, h23.x), fmaf(tf, g23.y - h23.y, h23.y));   // H1t
+        const float2 dd = make_float2(fmaf(tf, g23.z - h23.z, h23.z), fmaf(tf, g23.w - h23.w, h23.w));  // H1p
+        const float4 V = sspec[j];
+        const float2 v0 = make_float2(V.x, V.y), v1 = make_float2(V.z, V.w);
+        const float2 det = csub(cmul(a, dd), cmul(b, c));
+        const float sc = sqrtf(cabs2(a) * cabs2(dd)) + sqrtf(cabs2(b) * cabs2(c));
+        const float dd2 = cabs2(det);
+        if (dd2 > 1e-12f * sc * sc) {
+          const float inv = kScale / dd2;
+          const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
+          const float2 np = csub(cmul(a, v1), cmul(c, v0));
+          const float2 ct = cmulc(nt, det), cp = cmulc(np, det);
+          et = make_float2(ct.x * inv, ct.y * inv);
+          ep = make_float2(cp.x * inv, cp.y * inv);
+        } else {
+          sing = true;
+        }
+      }
+      E[j] = et;
+      E[M + j] = ep;
+    }
+    const bool any_sing = __syncthreads_or(sing);
+
+    // ---- pass 1: Q-point DFTs per (pol, r, ja) ----
+    {
+      const int r = tid / (2 * P);          // warp-uniform
+      const int pol = (tid / P) & 1;
+      const int ja = tid % P;
+      float2 x[Q];
+      const float2* Ep = E + pol * M;
+      switch (r) {
+        case 0: pass1_task<N_, 0>(Ep, ja, prm.t1, x); break;
+        case 1: pass1_task<N_, 1>(Ep, ja, prm.t1, x); break;
+        case 2: pass1_task<N_, 2>(Ep, ja, prm.t1, x); break;
+        default: pass1_task<N_, 3>(Ep, ja, prm.t1, x); break;
+      }
+      __syncthreads();   // every E read done: A may overwrite it
+      const int row = (prm.k_lo + ja) % P;
+      float2* dst = A + (pol * 4 + r) * PLN + row * LDA;
+      static_for<0, Q>([&](auto mb) { dst[mb] = x[mb]; });
+    }
+    __syncthreads();
+
+    // ---- pass 2: P-point DFTs, E-field, envelope, peak ----
+    const size_t pair = static_cast<size_t>(d) * prm.n_st + s;
+    float bv = -1.0f;
+    int bi = 0;
+    if constexpr (SPLIT == 1) {
+      const int r = tid & 3, mb = tid >> 2;
+      float pw[P];
+#pragma unroll
+      for (int pol = 0; pol < 2; ++pol) {
+        float2 y[P];
+        const float2* src = A + (pol * 4 + r) * PLN + mb;
+        static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
+        dft<P, +1>(y);
+        if (prm.efield) {
+          float* ef = prm.efield + (pair * 2 + pol) * N + tid;
+          static_for<0, P>([&](auto ma) { ef[T * ma] = y[ma].x; });
+        }
+        static_for<0, P>([&](auto ma) { pw[ma] = pol == 0 ? cabs2(y[ma]) : pw[ma] + cabs2(y[ma]); });
+      }
+      float* en = prm.envelope ? prm.envelope + pair * N + tid : nullptr;
+      static_for<0, P>([&](auto ma) {
+        const float v = sqrtf(pw[ma]);
+        if (en) en[T * ma] = v;
+        if (v > bv) { bv = v; bi = tid + T * ma; }
+      });
+    } else {
+      constexpr int TQ = 4 * Q;
+      const int pol = tid / TQ;             // warp-uniform
+      const int tq = tid % TQ;
+      const int r = tq & 3, mb = tq >> 2;
+      float2 y[P];
+      const float2* src = A + (pol * 4 + r) * PLN + mb;
+      static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
+      dft<P, +1>(y);
+      if (prm.efield) {
+        float* ef = prm.efield + (pair * 2 + pol) * N + tq;
+        static_for<0, P>([&](auto ma) { ef[TQ * ma] = y[ma].x; });
+      }
+      float pw[P];
+      static_for<0, P>([&](auto ma) {
+        pw[ma] = cabs2(y[ma]);
+        PWX[(pol * P + ma) * TQ + tq] = pw[ma];
+      });
+      __syncthreads();
+      float* en = prm.envelope ? prm.envelope + pair * N + tq : nullptr;
+      const float* other = PWX + (1 - pol) * P * TQ + tq;
+      if (pol == 0) {
+        static_for<0, P / 2>([&](auto ma) {
+          const float v = sqrtf(pw[ma] + other[ma * TQ]);
+          if (en) en[TQ * ma] = v;
+          if (v > bv) { bv = v; bi = tq + TQ * ma; }
+        });
+      } else {
+        static_for<P / 2, P>([&](auto ma) {
+          const float v = sqrtf(pw[ma] + other[ma * TQ]);
+          if (en) en[TQ * ma] = v;
+          if (v > bv) { bv = v; bi = tq + TQ * ma; }
+        });
+      }
+    }
+    // peak: max value, lowest index on ties
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { redv[tid >> 5] = bv; redi[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int w = 1; w < T / 32; ++w) {
+        if (redv[w] > bv || (redv[w] == bv && redi[w] < bi)) { bv = redv[w]; bi = redi[w]; }
+      }
+      if (bv < 0.f) { bv = 0.f; bi = 0; }
+      prm.peak_idx[pair] = bi;
+      prm.peak_amp[pair] = bv;
+      prm.peak_time[pair] = __dadd_rn(prm.t_start[s], __dmul_rn(static_cast<double>(bi), prm.dt_ns));
+      prm.status[pair] = di.st | (any_sing ? kStSingular : 0u);
+    }
+    __syncthreads();   // A, redv free for the next pair
+  }
+}
+
+// ---- K4: per-direction plane-wave residual (FP64) ----------------------------------------
+
+struct ResidualParams {
+  const double* pos;        // [S][3]
+  const double* dirs;       // [D][2]
+  const double* peak_time;  // [D][S]
+  double* residual;         // [D][S]
+  double* t0;               // [D]
+  double* chi2;             // [D]
+  double n_over_c;          // n_refr / c  [ns/m]
+  int n_st, n_dir;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
+  const int d = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (d >= p.n_dir) return;
+  const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
+  const double sz = sin(zen);
+  const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
+  const double* tp = p.peak_time + static_cast<size_t>(d) * p.n_st;
+  double acc = 0.0;
+  for (int s = lane; s < p.n_st; s += 32) {
+    const double* x = p.pos + 3 * s;
+    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
+    const double tau = -__dmul_rn(dot, p.n_over_c);
+    acc = __dadd_rn(acc, __dsub_rn(tp[s], tau));
+  }
+  const double mean = __ddiv_rn(warp_sum(acc), static_cast<double>(p.n_st));
+  double ss = 0.0;
+  double* res = p.residual + static_cast<size_t>(d) * p.n_st;
+  for (int s = lane; s < p.n_st; s += 32) {
+    const double* x = p.pos + 3 * s;
+    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
+    const double tau = -__dmul_rn(dot, p.n_over_c);
+    const double r = __dsub_rn(__dsub_rn(tp[s], tau), mean);
+    res[s] = r;
+    ss = __fma_rn(r, r, ss);
+  }
+  ss = warp_sum(ss);
+  if (lane == 0) {
+    p.t0[d] = mean;
+    p.chi2[d] = ss;
+  }
+}
+
+}  // namespace aerafold

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Cases: every supported trace length with ragged station/direction counts, the plain
+single event (10 stations x 2048 samples, 1 direction), the same at 4096 samples, and
+the 124-station x 64-direction scan at full size in the launch configuration the
+benchmark times (oracle on a sample of pairs there, plus properties checked for all
+pairs). Edge cases: one pair, non-finite and out-of-table directions, a singular antenna,
+peaks-only mode, host-buffer entry point, determinism, argument validation.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_07733_gb300 import synth
+from parity_util import check_event, check_pairs, check_times, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1507_07733_gb300 import binding
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pat():
+    return synth.make_pattern()
+
+
+@pytest.fixture(scope="module")
+def pid(ctx, pat):
+    return ctx.load_pattern(pat)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_gpu(ctx, pid, ev, traces_out=True, n_refr=1.0):
+    out = ctx.unfold(pid, _dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns), _dev(ev.dirs_rad),
+                     fs_hz=ev.fs_hz, refractive_index=n_refr, traces_out=traces_out, sync=True)
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("n,s,d", [(1024, 5, 3), (2048, 7, 5), (4096, 3, 2), (2048, 1, 1), (1024, 13, 9)])
+def test_parity_full_event(ctx, pat, pid, n, s, d):
+    rng = np.random.default_rng(n + 10 * s + d)
+    ev = synth.make_event(s, n, synth.random_directions(d, rng), seed_key=n + s)
+    gpu = run_gpu(ctx, pid, ev)
+    ref = oracle.unfold_event(pat, ev)
+    check_event(gpu, ref, ev)
+
+
+def test_parity_plain_single_event(ctx, pat, pid):
+    ev = synth.single_event(2048)
+    gpu = run_gpu(ctx, pid, ev)
+    ref = oracle.unfold_event(pat, ev)
+    check_event(gpu, ref, ev)
+
+
+def test_parity_single_event_4096(ctx, pat, pid):
+    ev = synth.single_event(4096)
+    gpu = run_gpu(ctx, pid, ev)
+    ref = oracle.unfold_event(pat, ev)
+    check_event(gpu, ref, ev)
+
+
+def test_parity_direction_scan_full_size_sampled(ctx, pat, pid):
+    ev = synth.direction_scan()
+    gpu = run_gpu(ctx, pid, ev)
+    S, D, N = ev.n_stations, ev.n_dirs, ev.n_samples
+    rng = np.random.default_rng(2)
+    q = np.concatenate([[0, S * D - 1, S - 1, (D - 1) * S], rng.choice(S * D, 60, replace=False)])
+    di, si = q // S, q % S
+    ref = oracle.unfold_sample(pat, ev, si, di)
+    sub = {k: gpu[k][di, si] for k in ("efield", "envelope", "peak_idx", "peak_amp", "status")}
+    check_pairs(sub, ref, N)
+    check_times(gpu["peak_time_ns"][di, si], ref["peak_time_ns"], "peak time (sample)")
+    # properties that hold for every pair
+    env = gpu["envelope"]
+    amp = gpu["peak_amp"]
+    idx = gpu["peak_idx"]
+    assert np.all(np.take_along_axis(env, idx[..., None].astype(np.int64), axis=2)[..., 0] == amp)
+    assert np.all(env.max(axis=2) == amp)
+    first = np.argmax(env == amp[..., None], axis=2)
+    assert np.array_equal(first, idx)
+    assert np.all(gpu["status"] == 0)
+    # residuals, t0 and chi2 of every direction from the GPU's own peak times
+    for d in range(D):
+        r, t0, chi2 = oracle.residual(ev.pos_m, gpu["peak_time_ns"][d], *ev.dirs_rad[d])
+        check_times(gpu["residual_ns"][d], r, "residual")
+        check_times(gpu["t0_ns"][d], t0, "t0")
+        assert abs(gpu["chi2"][d] - chi2) <= 1e-9 * max(chi2, 1.0)
+
+
+def test_edge_directions(ctx, pat, pid):
+    dirs = np.array([[math.radians(30), math.radians(45)], [float("nan"), 0.1], [0.2, float("inf")],
+                     [math.radians(97.0), 1.0], [-0.05, 2.0], [math.radians(20), -7.5],
+                     [math.radians(59.9), 4 * math.pi + 0.3], [math.radians(90), math.radians(355)]])
+    ev = synth.make_event(4, 2048, dirs, seed_key=21)
+    gpu = run_gpu(ctx, pid, ev)
+    ref = oracle.unfold_event(pat, ev)
+    check_event(gpu, ref, ev)
+    assert np.all(gpu["status"][1:3] == oracle.ST_BAD_DIR)
+    assert np.all(gpu["efield"][1:3] == 0) and np.all(gpu["peak_idx"][1:3] == 0)
+    assert np.all(gpu["status"][3:5] & oracle.ST_ZEN_CLAMP)
+
+
+def test_singular_antenna(ctx):
+    pat = synth.make_flat_pattern(np.array([[1.0, 2.0], [0.5, 1.0]]))   # rank one everywhere
+    pid = ctx.load_pattern(pat)
+    ev = synth.make_event(3, 1024, synth.scan_directions(2, 2), seed_key=22)
+    gpu = run_gpu(ctx, pid, ev)
+    assert np.all(gpu["status"] == oracle.ST_SINGULAR)
+    assert np.all(gpu["efield"] == 0) and np.all(gpu["envelope"] == 0)
+    ref = oracle.unfold_event(pat, ev)
+    assert np.array_equal(ref["status"], gpu["status"].astype(np.uint32))
+
+
+def test_peaks_only_matches_full(ctx, pid):
+    ev = synth.make_event(9, 2048, synth.scan_directions(3, 3), seed_key=23)
+    full = run_gpu(ctx, pid, ev)
+    peaks = run_gpu(ctx, pid, ev, traces_out=False)
+    for k in ("peak_idx", "peak_amp", "peak_time_ns", "residual_ns", "t0_ns", "chi2", "status"):
+        assert np.array_equal(full[k], peaks[k]), k
+
+
+def test_host_entry_point_matches_device(ctx, pid):
+    ev = synth.make_event(6, 4096, synth.scan_directions(2, 3), seed_key=24)
+    dev = run_gpu(ctx, pid, ev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    host = ctx.unfold_host(pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+    for k, v in dev.items():
+        assert np.array_equal(v, host[k].numpy()), k
+
+
+def test_deterministic(ctx, pid):
+    ev = synth.make_event(17, 1024, synth.scan_directions(4, 5), seed_key=25)
+    a = run_gpu(ctx, pid, ev)
+    b = run_gpu(ctx, pid, ev)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_refractive_index(ctx, pat, pid):
+    ev = synth.make_event(8, 1024, synth.scan_directions(2, 2), seed_key=26)
+    gpu = run_gpu(ctx, pid, ev, n_refr=1.000292)
+    for d in range(ev.n_dirs):
+        r, t0, chi2 = oracle.residual(ev.pos_m, gpu["peak_time_ns"][d], *ev.dirs_rad[d], n_refr=1.000292)
+        check_times(gpu["residual_ns"][d], r, "residual with n")
+
+
+def test_argument_validation(ctx, pid):
+    from paper_1507_07733_gb300 import binding
+    ev = synth.make_event(2, 1024, synth.scan_directions(1, 2), seed_key=27)
+    tr, pos, ts, dirs = _dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns), _dev(ev.dirs_rad)
+    with pytest.raises(binding.ArError) as e:
+        ctx.unfold(pid, _dev(np.zeros((2, 2, 512), np.float32)), pos, ts, dirs)
+    assert e.value.status == 2
+    with pytest.raises(binding.ArError) as e:
+        ctx.unfold(pid + 100, tr, pos, ts, dirs)
+    assert e.value.status == 3
+    with pytest.raises(binding.ArError) as e:
+        ctx.unfold(pid, tr, pos, ts, dirs, fs_hz=100e6)   # 80 MHz above Nyquist
+    assert e.value.status == 1
+    out, st = binding.alloc_outputs(2, 2, 1024)
+    st.peak_idx = None
+    with pytest.raises(binding.ArError) as e:
+        binding.ar_unfold(ctx.h, binding.make_event(pid, tr, pos, ts, dirs), st)
+    assert e.value.status == 1
