@@ -119,7 +119,8 @@ ar_status ar_create(ar_ctx** ctx, const ar_config* cfg);
 ar_status ar_destroy(ar_ctx* ctx);
 
 /* Message of the last failing call on ctx ("" if none). Valid until the next call on ctx.
- * ctx NULL gives the message of the last ar_create failure in this process. */
+ * ctx NULL gives the message of the last failing ar_create or ar_unfold_noalloc in this
+ * process. */
 const char* ar_last_error(const ar_ctx* ctx);
 
 /* Name of a status code. */
@@ -167,6 +168,31 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
  * residual. Errors: AR_ERR_INVALID_ARG (NULL, or no timed ar_unfold yet), AR_ERR_CUDA. */
 ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable);
 ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
+
+/* ar_unfold without any device allocation, for callers that cannot call cudaMalloc: a
+ * real-time acquisition loop whose device memory map is fixed after start-up, or a plug-in
+ * running inside another program's CUDA context and memory pool. The paper has no
+ * counterpart; it is an integration aid of this library.
+ *
+ * Same computation, conventions and output layouts as ar_unfold, with no context: the
+ * caller passes the pattern descriptor and a DEVICE pointer to its VEL table (layout of
+ * ar_load_pattern, 16-byte aligned; ev->pattern_id is ignored), the event's device arrays
+ * and the device outputs. Everything else the kernels need (station spectra, twiddle and
+ * frequency-cell tables, the error word) lives in one fixed 4 MiB array inside the library,
+ * present on every GPU that loads it until the process exits.
+ *  - Limit: n_stations x n_samples <= 1,000,000 (e.g. 488 stations of 2048 samples);
+ *    larger events return AR_ERR_INVALID_ARG and a message naming the limit.
+ *  - Set-up: the first call on a device (with that device current) looks up the array's
+ *    device address and sets kernel attributes; make that first call before any stream
+ *    capture.
+ *  - The array is shared by every call and keeps the last call's contents; each call clears
+ *    the error word and rewrites the tables before use. Calls whose work overlaps on the GPU
+ *    (different streams, or different host threads, without ordering) race on the array.
+ *  - Asynchronous on stream; there is no context to report device-side errors afterwards.
+ *  - Errors: AR_ERR_INVALID_ARG, AR_ERR_UNSUPPORTED_N, AR_ERR_CUDA; the message is
+ *    ar_last_error(NULL). */
+ar_status ar_unfold_noalloc(const ar_pattern_desc* desc, const float* device_table, const ar_event* ev,
+                            const ar_outputs* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,8 @@ AR_STATUS_BAD_DIR = 4
 
 #: every symbol include/aerafold.h declares
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
-            "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times"]
+            "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
+            "ar_unfold_noalloc"]
 
 
 class LibraryMissing(RuntimeError):
@@ -96,6 +97,8 @@ def load(path: str | None = None):
         L.ar_unfold_host.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
         L.ar_set_profiling.argtypes = [vp, i32]
         L.ar_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.ar_unfold_noalloc.argtypes = [ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(ar_event),
+                                        ctypes.POINTER(ar_outputs), vp]
         for name in EXPORTED:
             if name not in ("ar_last_error", "ar_status_string"):
                 getattr(L, name).restype = ctypes.c_int
@@ -165,6 +168,14 @@ def ar_kernel_times(ctx):
     ms = (ctypes.c_float * 3)()
     _check(ctx, load().ar_kernel_times(ctx, ms))
     return tuple(ms)
+
+
+def ar_unfold_noalloc(desc: dict, device_table_ptr: int, ev: ar_event, out: ar_outputs, stream: int = 0) -> None:
+    """The allocation-free entry point: ``device_table_ptr`` is the caller's device copy of the
+    VEL table; no context is involved."""
+    d = ar_pattern_desc(**desc)
+    _check(None, load().ar_unfold_noalloc(ctypes.byref(d), ctypes.c_void_p(device_table_ptr), ctypes.byref(ev),
+                                          ctypes.byref(out), ctypes.c_void_p(stream)))
 
 
 # ---- PyTorch-facing helpers ----------------------------------------------------------

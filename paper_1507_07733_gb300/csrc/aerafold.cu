@@ -548,3 +548,236 @@ ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
 }
 
 }  // extern "C"
+
+// ---- allocation-free entry point ----------------------------------------------------------
+//
+// For callers that cannot allocate device memory at all: code that runs inside a host that
+// forbids cudaMalloc after start-up (a real-time data-taking loop with a fixed memory map, a
+// plug-in living in someone else's CUDA context and memory pool). ar_unfold_noalloc runs the
+// same three kernels as ar_unfold, but every buffer the library needs beyond the caller's
+// inputs and outputs -- the station spectra, the twiddle and frequency-cell tables, the error
+// word -- lives in the file-scope array below. The array exists once per GPU that loads the
+// library and stays allocated until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4u << 20;          // 4 MiB per device
+constexpr size_t kNoAllocTablesBytes = 96u << 10;          // err word + T1 + TWF + WN + cells
+constexpr long long kNoAllocMaxStationSamples = 1000000;   // stations x samples per channel
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char* scratch = nullptr;   // device address of g_noalloc_scratch on this device
+  int num_sms = 0;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// failures are reported through the process-wide message that ar_last_error(NULL) returns
+ar_status noalloc_fail(ar_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> lk(g_create_mu);
+  g_create_error = buf;
+  return st;
+}
+
+#define AR_NA_CUDA(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return noalloc_fail(AR_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Twiddle and frequency-cell tables of one trace length, computed on the device in FP64
+// (sincospi) and rounded once to float; the same definitions as the host tables of ar_unfold.
+template <int N_>
+__global__ void noalloc_tables_kernel(float2* t1, float2* twf, float2* wn, int2* binf, int k_lo, double fs,
+                                      double f0, double df, int n_f) {
+  using L = Layout<N_>;
+  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P;
+  const int total = 4 * Q * P + Q * P + N + M;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    double s, c;
+    if (i < 4 * Q * P) {
+      const int r = i / (Q * P), mb = (i / P) % Q, ja = i % P;
+      const long t = (static_cast<long>(k_lo + ja) * (r + 4 * mb)) % N;
+      sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
+      t1[i] = make_float2(static_cast<float>(c), static_cast<float>(s));
+    } else if (i < 5 * Q * P) {
+      const int j = i - 4 * Q * P, q = j / P, p = j % P;
+      const long t = (static_cast<long>(p) * q) % M;
+      sincospi(2.0 * static_cast<double>(t) / M, &s, &c);
+      twf[j] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    } else if (i < 5 * Q * P + N) {
+      const int t = i - 5 * Q * P;
+      sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
+      wn[t] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+    } else {
+      const int j = i - 5 * Q * P - N, k = k_lo + j;
+      const double f = __ddiv_rn(__dmul_rn(static_cast<double>(k), fs), static_cast<double>(N));
+      if (!(f >= kBandLoHz && f <= kBandHiHz)) {
+        binf[j] = make_int2(-1, 0);
+        continue;
+      }
+      double u = __ddiv_rn(__dsub_rn(f, f0), df);
+      if (u < 0.0) u = 0.0;
+      if (u > static_cast<double>(n_f - 1)) u = static_cast<double>(n_f - 1);
+      int cell = static_cast<int>(floor(u));
+      if (cell > n_f - 2) cell = n_f - 2;
+      binf[j] = make_int2(cell, __float_as_int(static_cast<float>(__dsub_rn(u, static_cast<double>(cell)))));
+    }
+  }
+}
+
+// once per device, with that device current: the device address of the scratch array
+ar_status noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(AR_ERR_CUDA, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    AR_NA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    AR_NA_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t sp1 = sizeof(float2) * (Layout<1024>::N + 4 * Layout<1024>::PLN);
+    const size_t sp2 = sizeof(float2) * (Layout<2048>::N + 4 * Layout<2048>::PLN);
+    const size_t sp4 = sizeof(float2) * (Layout<4096>::N + 4 * Layout<4096>::PLN);
+    AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp1)));
+    AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp2)));
+    AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp4)));
+    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<1024>::total(kMaxFreqNodes))));
+    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<2048>::total(kMaxFreqNodes))));
+    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<4096>::total(kMaxFreqNodes))));
+    d.scratch = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = &d;
+  return AR_OK;
+}
+
+template <int N_>
+ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const float* table, const ar_event* ev,
+                         const ar_outputs* out, int k_lo, cudaStream_t stream) {
+  using L = Layout<N_>;
+  unsigned char* base = nd.scratch;
+  unsigned* err = reinterpret_cast<unsigned*>(base);
+  float2* t1 = reinterpret_cast<float2*>(base + 256);
+  float2* twf = reinterpret_cast<float2*>(base + 256 + (32u << 10));
+  float2* wn = reinterpret_cast<float2*>(base + 256 + (40u << 10));
+  int2* binf = reinterpret_cast<int2*>(base + 256 + (72u << 10));
+  float4* spec = reinterpret_cast<float4*>(base + kNoAllocTablesBytes);
+  // the error word must start at zero; the tables are rewritten by every call
+  AR_NA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), stream));
+  noalloc_tables_kernel<N_><<<40, 256, 0, stream>>>(t1, twf, wn, binf, k_lo, ev->fs_hz, pd->f0_hz, pd->df_hz,
+                                                     pd->n_freq);
+  AR_NA_CUDA(cudaGetLastError());
+  SpectrumParams sp{ev->traces, spec, twf, wn, k_lo};
+  station_spectrum_kernel<N_><<<ev->n_stations, L::T, sizeof(float2) * (L::N + 4 * L::PLN), stream>>>(sp);
+  AR_NA_CUDA(cudaGetLastError());
+  UnfoldParams up{};
+  up.spec = spec;
+  up.table = reinterpret_cast<const float2*>(table);
+  up.binf = binf;
+  up.t1 = t1;
+  up.dirs = ev->dirs_rad;
+  up.t_start = ev->t_start_ns;
+  up.efield = out->efield;
+  up.envelope = out->envelope;
+  up.peak_idx = out->peak_idx;
+  up.peak_amp = out->peak_amp;
+  up.peak_time = out->peak_time_ns;
+  up.status = out->status;
+  up.err = err;
+  up.zen0 = pd->zen0_rad;
+  up.dzen = pd->dzen_rad;
+  up.az0 = pd->az0_rad;
+  up.daz = pd->daz_rad;
+  up.dt_ns = 1e9 / ev->fs_hz;
+  up.n_zen = pd->n_zen;
+  up.n_az = pd->n_az;
+  up.n_f = pd->n_freq;
+  up.n_st = ev->n_stations;
+  up.n_dir = ev->n_dirs;
+  up.k_lo = k_lo;
+  up.total_pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
+  const size_t smem = UnfoldSmem<N_>::total(pd->n_freq);
+  int per_sm = 0;
+  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T, smem));
+  if (per_sm < 1) return noalloc_fail(AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM", N_);
+  const long long grid = std::min<long long>(static_cast<long long>(per_sm) * nd.num_sms, up.total_pairs);
+  unfold_kernel<N_><<<static_cast<int>(grid), L::T, smem, stream>>>(up);
+  AR_NA_CUDA(cudaGetLastError());
+  ResidualParams rp{};
+  rp.pos = ev->pos_m;
+  rp.dirs = ev->dirs_rad;
+  rp.peak_time = out->peak_time_ns;
+  rp.residual = out->residual_ns;
+  rp.t0 = out->t0_ns;
+  rp.chi2 = out->chi2;
+  rp.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  rp.n_st = ev->n_stations;
+  rp.n_dir = ev->n_dirs;
+  residual_kernel<<<(ev->n_dirs + 3) / 4, 128, 0, stream>>>(rp);
+  AR_NA_CUDA(cudaGetLastError());
+  return AR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const ar_event* ev,
+                            const ar_outputs* out, void* stream) {
+  if (!pd || !table) return noalloc_fail(AR_ERR_INVALID_ARG, "pattern descriptor and table must not be NULL");
+  if (reinterpret_cast<uintptr_t>(table) % 16 != 0)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "the VEL table must be 16-byte aligned");
+  if (pd->n_zen < 2 || pd->n_az < 2 || pd->n_freq < 2 || pd->n_freq > kMaxFreqNodes || !(pd->dzen_rad > 0) ||
+      !(pd->daz_rad > 0) || !(pd->df_hz > 0) ||
+      std::fabs(pd->n_az * pd->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "bad pattern descriptor");
+  if (!ev || !out) return noalloc_fail(AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+  if (ev->n_stations < 1 || ev->n_dirs < 1 || ev->n_dirs > (1 << 20))
+    return noalloc_fail(AR_ERR_INVALID_ARG, "n_stations and n_dirs must be >= 1 (n_dirs <= 2^20)");
+  if (ev->n_samples != 1024 && ev->n_samples != 2048 && ev->n_samples != 4096)
+    return noalloc_fail(AR_ERR_UNSUPPORTED_N, "n_samples=%d: supported lengths are 1024, 2048, 4096",
+                        ev->n_samples);
+  if (static_cast<long long>(ev->n_stations) * ev->n_samples > kNoAllocMaxStationSamples)
+    return noalloc_fail(AR_ERR_INVALID_ARG,
+                        "n_stations x n_samples = %lld exceeds the fixed scratch of ar_unfold_noalloc "
+                        "(at most %lld, e.g. 488 stations of 2048 samples)",
+                        static_cast<long long>(ev->n_stations) * ev->n_samples, kNoAllocMaxStationSamples);
+  if (!ev->traces || !ev->pos_m || !ev->t_start_ns || !ev->dirs_rad ||
+      reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "event arrays must be non-NULL, traces 16-byte aligned");
+  if (!out->peak_idx || !out->peak_amp || !out->peak_time_ns || !out->residual_ns || !out->t0_ns || !out->chi2 ||
+      !out->status)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
+  if (!(ev->fs_hz > 0.0)) return noalloc_fail(AR_ERR_INVALID_ARG, "fs_hz must be positive");
+  int lo, cnt, hi;
+  band_window(ev->n_samples, ev->fs_hz, &lo, &cnt, &hi);
+  if (cnt < 1 || cnt > ev->n_samples / 4 || lo + ev->n_samples / 4 > ev->n_samples / 2 || 2 * hi >= ev->n_samples)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "fs=%g Hz: the 30-80 MHz band must fit N/4 bins below Nyquist",
+                        ev->fs_hz);
+  int dev = 0;
+  AR_NA_CUDA(cudaGetDevice(&dev));
+  NoAllocDevice* nd = nullptr;
+  ar_status st = noalloc_setup(dev, &nd);
+  if (st != AR_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (ev->n_samples) {
+    case 1024: return noalloc_launch<1024>(*nd, pd, table, ev, out, lo, s);
+    case 2048: return noalloc_launch<2048>(*nd, pd, table, ev, out, lo, s);
+    default: return noalloc_launch<4096>(*nd, pd, table, ev, out, lo, s);
+  }
+}
+
+}  // extern "C"
