@@ -4,7 +4,8 @@
 Workload (one step): the 124-station direction scan -- 124 stations x 2 channels x 2048
 float32 samples at 200 MHz, 64 candidate directions (zenith 0-60 deg x 8, azimuth 0-315 deg
 x 8), the 19 x 72 x 51 synthetic VEL table -- unfolded pair by pair through the C ABI
-(ar_unfold: station transform, fused unfold, residual). 7936 pairs per step.
+(ar_unfold: station transform, then the fused unfold with the per-direction residual).
+7936 pairs per step.
 
   value        pairs / s over the K timed steps (device time, CUDA events per step on the
                launching stream, L2 flushed by a 256 MiB write between steps, outside the
@@ -13,7 +14,8 @@ x 8), the 19 x 72 x 51 synthetic VEL table -- unfolded pair by pair through the 
                host->device copy, the kernels, and the device->host copy of every output
                inside each timed step (host wall clock)
   roofline     the fused unfold kernel: algorithmic bytes per launch / its mean duration
-               (CUDA events recorded by the library around it, same stream) vs measured HBM
+               (CUDA events recorded by the library around it, same stream) vs measured HBM;
+               roofline_alu the same duration against the FP32 issue peak
   cpu_baseline the FP64 oracle on a bounded sample of the same workload on the host cores
 
 --impl reference times the oracle alone (each step: one station x 16 directions of the
@@ -150,10 +152,11 @@ class ClockSampler:
 # ---- algorithmic work -----------------------------------------------------------------
 
 def unfold_bytes_per_launch(S: int, D: int, N: int, n_f: int) -> int:
-    """Bytes the fused unfold kernel must move: writes of E-field (8N), envelope (4N), peak
-    index/amplitude/time/status (20 B) per pair; reads of each station's band spectrum
-    (N/4 bins x 16 B) and each direction's four corner slabs (4 x n_f x 32 B) once."""
-    return S * D * (12 * N + 20) + S * (N // 4) * 16 + D * 4 * n_f * 32
+    """Bytes the fused unfold kernel must move: per pair, writes of E-field (8N), envelope (4N),
+    peak index/amplitude/time, status and residual (28 B); per station, reads of its band
+    spectrum (N/4 bins x 16 B), position and window start (32 B); per direction, reads of its
+    four corner slabs (4 x n_f x 32 B) and angles (16 B) and writes of t0 and chi2 (16 B)."""
+    return S * D * (12 * N + 28) + S * ((N // 4) * 16 + 32) + D * (4 * n_f * 32 + 32)
 
 
 def unfold_flops_per_pair(N: int, D: int) -> float:
@@ -251,7 +254,6 @@ def run_gpu(args):
     binding.ar_sync(ctx.h, sp)
     k3 = statistics.mean(m[1] for m in k_ms)
     k1 = statistics.mean(m[0] for m in k_ms)
-    k4 = statistics.mean(m[2] for m in k_ms)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs")
@@ -312,8 +314,8 @@ def run_gpu(args):
                          "kernel": "unfold_kernel<2048>", "kernel_ms": round(k3, 5),
                          "algorithmic_bytes_per_launch": nbytes},
             "roofline_alu": alu,
-            "kernel_ms": {"station_spectrum": round(k1, 5), "unfold": round(k3, 5), "residual": round(k4, 5)},
-            "gpu_launches": 3 * args.steps,
+            "kernel_ms": {"station_spectrum": round(k1, 5), "unfold_with_residual": round(k3, 5)},
+            "gpu_launches": 2 * args.steps,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(h0, h1),

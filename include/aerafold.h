@@ -143,9 +143,9 @@ ar_status ar_prepare(ar_ctx* ctx, int32_t n_samples, double fs_hz, int32_t patte
 
 /* Unfold every (station, direction) pair of ev into out, asynchronously on stream
  * (a cudaStream_t; NULL = the legacy default stream). All pointers are device pointers.
- * Three kernels run in order: the forward transform of each station's two channels, the
- * fused per-pair interpolation + solve + inverse transform + envelope + peak, and the
- * per-direction plane-wave residual. Validation errors are returned before any launch;
+ * Two kernels run in order: the forward transform of each station's two channels, then the
+ * fused per-pair interpolation + solve + inverse transform + envelope + peak, in which the
+ * CTA that finishes a direction's last pair also computes its plane-wave residual. Validation errors are returned before any launch;
  * a device-side error is reported by the next ar_sync on this context.
  * If the shape was not prepared, the first call allocates (synchronously).
  * Errors: AR_ERR_INVALID_ARG, AR_ERR_UNSUPPORTED_N, AR_ERR_NO_PATTERN,
@@ -163,9 +163,11 @@ ar_status ar_sync(ar_ctx* ctx, void* stream);
 ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream);
 
 /* Per-kernel timing. While enabled, ar_unfold records CUDA events on its stream around each
- * of its three kernels. ar_kernel_times waits for the last ar_unfold's events and writes
- * the durations in milliseconds: ms[0] station transform, ms[1] fused unfold, ms[2]
- * residual. Errors: AR_ERR_INVALID_ARG (NULL, or no timed ar_unfold yet), AR_ERR_CUDA. */
+ * of its kernels (which keeps the second kernel from starting before the first ends).
+ * ar_kernel_times waits for the last ar_unfold's events and writes the durations in
+ * milliseconds: ms[0] station transform, ms[1] fused unfold (including the per-direction
+ * residual), ms[2] always 0 (kept for layout stability).
+ * Errors: AR_ERR_INVALID_ARG (NULL, or no timed ar_unfold yet), AR_ERR_CUDA. */
 ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable);
 ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
 
@@ -178,10 +180,12 @@ ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
  * caller passes the pattern descriptor and a DEVICE pointer to its VEL table (layout of
  * ar_load_pattern, 16-byte aligned; ev->pattern_id is ignored), the event's device arrays
  * and the device outputs. Everything else the kernels need (station spectra, twiddle and
- * frequency-cell tables, the error word) lives in one fixed 4 MiB array inside the library,
+ * frequency-cell tables, per-direction counters, the error word) lives in one fixed 4 MiB
+ * array inside the library,
  * present on every GPU that loads it until the process exits.
- *  - Limit: n_stations x n_samples <= 1,000,000 (e.g. 488 stations of 2048 samples);
- *    larger events return AR_ERR_INVALID_ARG and a message naming the limit.
+ *  - Limits: n_stations x n_samples <= 983,040 (240 stations of 4096 samples, 480 of 2048,
+ *    960 of 1024) and n_dirs <= 4096; larger events return AR_ERR_INVALID_ARG and a
+ *    message naming the limit.
  *  - Set-up: the first call on a device (with that device current) looks up the array's
  *    device address and sets kernel attributes; make that first call before any stream
  *    capture.

@@ -61,6 +61,8 @@ struct ar_ctx {
   std::map<std::pair<int, int>, KernelCfg> unfold_cfg;                 // (N, n_f)
   float4* spec = nullptr;
   size_t spec_bytes = 0;
+  unsigned* dir_done = nullptr;   // [max directions] completion counters of the fused residual
+  size_t dir_cap = 0;
   unsigned* d_err = nullptr;
   // device staging for ar_unfold_host
   std::vector<std::pair<void*, size_t>> stage;   // slots, grown on demand
@@ -111,6 +113,17 @@ float2 unit(long t, long n, int sign) {   // exp(sign * 2 pi i t / n), t reduced
   if (t < 0) t += n;
   const double a = 2.0 * M_PI * static_cast<double>(t) / static_cast<double>(n);
   return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(sign * std::sin(a)));
+}
+
+// the pass-1 pre-twiddles exp(2 pi i jb r / 4Q) into the kernels' constant tables (current device)
+cudaError_t upload_pretwiddles() {
+  float2 a[4][32], b[4][16];
+  for (int r = 0; r < 4; ++r) {
+    for (int j = 0; j < 32; ++j) a[r][j] = unit(static_cast<long>(j) * r, 128, +1);
+    for (int j = 0; j < 16; ++j) b[r][j] = unit(static_cast<long>(j) * r, 64, +1);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_pre32, a, sizeof a);
+  return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_pre16, b, sizeof b);
 }
 
 template <int N_>
@@ -183,6 +196,21 @@ ar_status get_bin_table(ar_ctx* ctx, int n, double fs, int pid, int k_lo, int2**
   return AR_OK;
 }
 
+ar_status ensure_dirs(ar_ctx* ctx, size_t n_dir) {
+  if (n_dir <= ctx->dir_cap) return AR_OK;
+  if (ctx->dir_done) {
+    AR_CUDA(ctx, cudaDeviceSynchronize());
+    AR_CUDA(ctx, cudaFree(ctx->dir_done));
+    ctx->dir_done = nullptr;
+    ctx->dir_cap = 0;
+  }
+  const size_t cap = std::max<size_t>(n_dir, 256);
+  AR_CUDA(ctx, cudaMalloc(&ctx->dir_done, cap * sizeof(unsigned)));
+  AR_CUDA(ctx, cudaMemset(ctx->dir_done, 0, cap * sizeof(unsigned)));
+  ctx->dir_cap = cap;
+  return AR_OK;
+}
+
 ar_status ensure_spec(ar_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->spec_bytes) return AR_OK;
   if (ctx->spec) {
@@ -210,9 +238,8 @@ ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
                                                                kc.smem));
     if (per_sm < 1) return fail(ctx, AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM (smem %zu)", N_, kc.smem);
     kc.grid = per_sm * ctx->num_sms;
-    const size_t sp_smem = sizeof(float2) * (Layout<N_>::N + 4 * Layout<N_>::PLN);
     AR_CUDA(ctx, cudaFuncSetAttribute(station_spectrum_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(sp_smem)));
+                                      static_cast<int>(SpectrumSmem<N_>::TOTAL)));
     it = ctx->unfold_cfg.emplace(key, kc).first;
   }
   *out = &it->second;
@@ -255,65 +282,97 @@ ar_status resolve(ar_ctx* ctx, int n, double fs, int pid, int max_st, Resolved* 
   return ensure_spec(ctx, sizeof(float4) * static_cast<size_t>(n / 4) * static_cast<size_t>(max_st));
 }
 
-template <int N_>
-ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, const Resolved& rs,
-                     cudaStream_t stream) {
-  using L = Layout<N_>;
-  const PatternDev& pat = ctx->patterns[ev->pattern_id];
-  SpectrumParams sp{ev->traces, ctx->spec, rs.lt->twf, rs.lt->wn, rs.k_lo};
-  const size_t sp_smem = sizeof(float2) * (L::N + 4 * L::PLN);
-  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[0], stream));
-  station_spectrum_kernel<N_><<<ev->n_stations, L::T, sp_smem, stream>>>(sp);
-  AR_CUDA(ctx, cudaGetLastError());
-  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[1], stream));
+ar_status resolve_dirs(ar_ctx* ctx, int n_dir) { return ensure_dirs(ctx, static_cast<size_t>(n_dir)); }
 
+// Launch with programmatic dependent launch allowed: the kernel may start while the previous
+// kernel in the stream finishes; it waits (griddepcontrol.wait) before touching its results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+struct PathBuffers {      // library-side buffers one launch of the path uses
+  float4* spec;
+  unsigned* dir_done;
+  unsigned* err;
+  const float2* t1;
+  const float2* twf;
+  const float2* wn;
+  const int2* binf;
+};
+
+template <int N_>
+cudaError_t launch_path(const PathBuffers& b, const ar_pattern_desc& pd, const float2* table, const ar_event* ev,
+                        const ar_outputs* out, int k_lo, int grid_cap, cudaStream_t stream,
+                        cudaEvent_t* evs /* 3 events or null */) {
+  using L = Layout<N_>;
+  SpectrumParams sp{ev->traces, b.spec, b.twf, b.wn, b.dir_done, ev->n_dirs, k_lo};
+  cudaError_t e;
+  if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, ev->n_stations, L::T, SpectrumSmem<N_>::TOTAL, stream, sp)) !=
+      cudaSuccess)
+    return e;
+  if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
   UnfoldParams up{};
-  up.spec = ctx->spec;
-  up.table = pat.table;
-  up.binf = rs.binf;
-  up.t1 = rs.lt->t1;
+  up.spec = b.spec;
+  up.table = table;
+  up.binf = b.binf;
+  up.t1 = b.t1;
   up.dirs = ev->dirs_rad;
   up.t_start = ev->t_start_ns;
+  up.pos = ev->pos_m;
   up.efield = out->efield;
   up.envelope = out->envelope;
   up.peak_idx = out->peak_idx;
   up.peak_amp = out->peak_amp;
   up.peak_time = out->peak_time_ns;
   up.status = out->status;
-  up.err = ctx->d_err;
-  up.zen0 = pat.desc.zen0_rad;
-  up.dzen = pat.desc.dzen_rad;
-  up.az0 = pat.desc.az0_rad;
-  up.daz = pat.desc.daz_rad;
+  up.residual = out->residual_ns;
+  up.t0 = out->t0_ns;
+  up.chi2 = out->chi2;
+  up.err = b.err;
+  up.dir_done = b.dir_done;
+  up.zen0 = pd.zen0_rad;
+  up.dzen = pd.dzen_rad;
+  up.az0 = pd.az0_rad;
+  up.daz = pd.daz_rad;
   up.dt_ns = 1e9 / ev->fs_hz;
-  up.n_zen = pat.desc.n_zen;
-  up.n_az = pat.desc.n_az;
-  up.n_f = pat.desc.n_freq;
+  up.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  up.n_zen = pd.n_zen;
+  up.n_az = pd.n_az;
+  up.n_f = pd.n_freq;
   up.n_st = ev->n_stations;
   up.n_dir = ev->n_dirs;
-  up.k_lo = rs.k_lo;
+  up.k_lo = k_lo;
   up.total_pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
-  const long long grid = std::min<long long>(rs.kc->grid, up.total_pairs);
-  unfold_kernel<N_><<<static_cast<int>(grid), L::T, rs.kc->smem, stream>>>(up);
-  AR_CUDA(ctx, cudaGetLastError());
-  if (ctx->profiling) AR_CUDA(ctx, cudaEventRecord(ctx->ev[2], stream));
+  const long long grid = std::min<long long>(grid_cap, up.total_pairs);
+  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T, UnfoldSmem<N_>::total(pd.n_freq), stream,
+                      up)) != cudaSuccess)
+    return e;
+  if (evs && (e = cudaEventRecord(evs[2], stream)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
 
-  ResidualParams rp{};
-  rp.pos = ev->pos_m;
-  rp.dirs = ev->dirs_rad;
-  rp.peak_time = out->peak_time_ns;
-  rp.residual = out->residual_ns;
-  rp.t0 = out->t0_ns;
-  rp.chi2 = out->chi2;
-  rp.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
-  rp.n_st = ev->n_stations;
-  rp.n_dir = ev->n_dirs;
-  residual_kernel<<<(ev->n_dirs + 3) / 4, 128, 0, stream>>>(rp);
-  AR_CUDA(ctx, cudaGetLastError());
-  if (ctx->profiling) {
-    AR_CUDA(ctx, cudaEventRecord(ctx->ev[3], stream));
-    ctx->timed = true;
-  }
+template <int N_>
+ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, const Resolved& rs,
+                     cudaStream_t stream) {
+  const PatternDev& pat = ctx->patterns[ev->pattern_id];
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  cudaError_t e = launch_path<N_>(b, pat.desc, pat.table, ev, out, rs.k_lo, rs.kc->grid, stream,
+                                  ctx->profiling ? ctx->ev : nullptr);
+  if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  if (ctx->profiling) ctx->timed = true;
   return AR_OK;
 }
 
@@ -376,7 +435,7 @@ ar_status ar_create(ar_ctx** out, const ar_config* cfg) {
   ctx->cfg = c;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess || upload_pretwiddles() != cudaSuccess) {
     delete ctx;
     return create_fail(AR_ERR_OUT_OF_MEMORY, "context allocation failed");
   }
@@ -399,6 +458,7 @@ ar_status ar_destroy(ar_ctx* ctx) {
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   cudaFree(ctx->spec);
+  cudaFree(ctx->dir_done);
   cudaFree(ctx->d_err);
   delete ctx;
   return AR_OK;
@@ -454,6 +514,7 @@ ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void
   AR_CUDA(ctx, cudaSetDevice(ctx->device));
   Resolved rs;
   if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve_dirs(ctx, ev->n_dirs)) != AR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (ev->n_samples) {
     case 1024: return launch_all<1024>(ctx, ev, out, rs, s);
@@ -542,8 +603,10 @@ ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable) {
 ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
   if (!ctx) return AR_ERR_INVALID_ARG;
   if (!ms || !ctx->timed) return fail(ctx, AR_ERR_INVALID_ARG, "no timed ar_unfold to report");
-  AR_CUDA(ctx, cudaEventSynchronize(ctx->ev[3]));
-  for (int i = 0; i < 3; ++i) AR_CUDA(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+  AR_CUDA(ctx, cudaEventSynchronize(ctx->ev[2]));
+  AR_CUDA(ctx, cudaEventElapsedTime(&ms[0], ctx->ev[0], ctx->ev[1]));
+  AR_CUDA(ctx, cudaEventElapsedTime(&ms[1], ctx->ev[1], ctx->ev[2]));
+  ms[2] = 0.0f;   // the residual runs inside the unfold kernel
   return AR_OK;
 }
 
@@ -562,8 +625,9 @@ ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 4u << 20;          // 4 MiB per device
-constexpr size_t kNoAllocTablesBytes = 96u << 10;          // err word + T1 + TWF + WN + cells
-constexpr long long kNoAllocMaxStationSamples = 1000000;   // stations x samples per channel
+constexpr size_t kNoAllocTablesBytes = 112u << 10;         // err, counters, T1, TWF, WN, cells
+constexpr long long kNoAllocMaxStationSamples = 983040;    // stations x samples per channel
+constexpr int kNoAllocMaxDirs = 4096;                      // directions per event
 constexpr int kNoAllocMaxDevices = 64;
 
 }  // namespace
@@ -647,10 +711,11 @@ ar_status noalloc_setup(int dev, NoAllocDevice** out) {
   if (!d.ready) {
     void* p = nullptr;
     AR_NA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    AR_NA_CUDA(upload_pretwiddles());
     AR_NA_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t sp1 = sizeof(float2) * (Layout<1024>::N + 4 * Layout<1024>::PLN);
-    const size_t sp2 = sizeof(float2) * (Layout<2048>::N + 4 * Layout<2048>::PLN);
-    const size_t sp4 = sizeof(float2) * (Layout<4096>::N + 4 * Layout<4096>::PLN);
+    const size_t sp1 = SpectrumSmem<1024>::TOTAL;
+    const size_t sp2 = SpectrumSmem<2048>::TOTAL;
+    const size_t sp4 = SpectrumSmem<4096>::TOTAL;
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp1)));
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp2)));
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp4)));
@@ -669,65 +734,30 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
                          const ar_outputs* out, int k_lo, cudaStream_t stream) {
   using L = Layout<N_>;
   unsigned char* base = nd.scratch;
-  unsigned* err = reinterpret_cast<unsigned*>(base);
-  float2* t1 = reinterpret_cast<float2*>(base + 256);
-  float2* twf = reinterpret_cast<float2*>(base + 256 + (32u << 10));
-  float2* wn = reinterpret_cast<float2*>(base + 256 + (40u << 10));
-  int2* binf = reinterpret_cast<int2*>(base + 256 + (72u << 10));
-  float4* spec = reinterpret_cast<float4*>(base + kNoAllocTablesBytes);
-  // the error word must start at zero; the tables are rewritten by every call
-  AR_NA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), stream));
+  PathBuffers b{};
+  b.err = reinterpret_cast<unsigned*>(base);
+  b.dir_done = reinterpret_cast<unsigned*>(base + 256);                       // 16 KiB
+  float2* t1 = reinterpret_cast<float2*>(base + 256 + (16u << 10));           // 32 KiB
+  float2* twf = reinterpret_cast<float2*>(base + 256 + (48u << 10));          // 8 KiB
+  float2* wn = reinterpret_cast<float2*>(base + 256 + (56u << 10));           // 32 KiB
+  int2* binf = reinterpret_cast<int2*>(base + 256 + (88u << 10));             // 8 KiB
+  b.t1 = t1;
+  b.twf = twf;
+  b.wn = wn;
+  b.binf = binf;
+  b.spec = reinterpret_cast<float4*>(base + kNoAllocTablesBytes);
+  // the error word must start at zero (the direction counters are zeroed by the first
+  // kernel); the tables are rewritten by every call
+  AR_NA_CUDA(cudaMemsetAsync(b.err, 0, sizeof(unsigned), stream));
   noalloc_tables_kernel<N_><<<40, 256, 0, stream>>>(t1, twf, wn, binf, k_lo, ev->fs_hz, pd->f0_hz, pd->df_hz,
                                                      pd->n_freq);
   AR_NA_CUDA(cudaGetLastError());
-  SpectrumParams sp{ev->traces, spec, twf, wn, k_lo};
-  station_spectrum_kernel<N_><<<ev->n_stations, L::T, sizeof(float2) * (L::N + 4 * L::PLN), stream>>>(sp);
-  AR_NA_CUDA(cudaGetLastError());
-  UnfoldParams up{};
-  up.spec = spec;
-  up.table = reinterpret_cast<const float2*>(table);
-  up.binf = binf;
-  up.t1 = t1;
-  up.dirs = ev->dirs_rad;
-  up.t_start = ev->t_start_ns;
-  up.efield = out->efield;
-  up.envelope = out->envelope;
-  up.peak_idx = out->peak_idx;
-  up.peak_amp = out->peak_amp;
-  up.peak_time = out->peak_time_ns;
-  up.status = out->status;
-  up.err = err;
-  up.zen0 = pd->zen0_rad;
-  up.dzen = pd->dzen_rad;
-  up.az0 = pd->az0_rad;
-  up.daz = pd->daz_rad;
-  up.dt_ns = 1e9 / ev->fs_hz;
-  up.n_zen = pd->n_zen;
-  up.n_az = pd->n_az;
-  up.n_f = pd->n_freq;
-  up.n_st = ev->n_stations;
-  up.n_dir = ev->n_dirs;
-  up.k_lo = k_lo;
-  up.total_pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
-  const size_t smem = UnfoldSmem<N_>::total(pd->n_freq);
   int per_sm = 0;
-  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T, smem));
+  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T,
+                                                           UnfoldSmem<N_>::total(pd->n_freq)));
   if (per_sm < 1) return noalloc_fail(AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM", N_);
-  const long long grid = std::min<long long>(static_cast<long long>(per_sm) * nd.num_sms, up.total_pairs);
-  unfold_kernel<N_><<<static_cast<int>(grid), L::T, smem, stream>>>(up);
-  AR_NA_CUDA(cudaGetLastError());
-  ResidualParams rp{};
-  rp.pos = ev->pos_m;
-  rp.dirs = ev->dirs_rad;
-  rp.peak_time = out->peak_time_ns;
-  rp.residual = out->residual_ns;
-  rp.t0 = out->t0_ns;
-  rp.chi2 = out->chi2;
-  rp.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
-  rp.n_st = ev->n_stations;
-  rp.n_dir = ev->n_dirs;
-  residual_kernel<<<(ev->n_dirs + 3) / 4, 128, 0, stream>>>(rp);
-  AR_NA_CUDA(cudaGetLastError());
+  AR_NA_CUDA(launch_path<N_>(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo, per_sm * nd.num_sms,
+                             stream, nullptr));
   return AR_OK;
 }
 
@@ -745,15 +775,15 @@ ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const
       std::fabs(pd->n_az * pd->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
     return noalloc_fail(AR_ERR_INVALID_ARG, "bad pattern descriptor");
   if (!ev || !out) return noalloc_fail(AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
-  if (ev->n_stations < 1 || ev->n_dirs < 1 || ev->n_dirs > (1 << 20))
-    return noalloc_fail(AR_ERR_INVALID_ARG, "n_stations and n_dirs must be >= 1 (n_dirs <= 2^20)");
+  if (ev->n_stations < 1 || ev->n_dirs < 1 || ev->n_dirs > kNoAllocMaxDirs)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "n_stations must be >= 1 and n_dirs in [1, %d]", kNoAllocMaxDirs);
   if (ev->n_samples != 1024 && ev->n_samples != 2048 && ev->n_samples != 4096)
     return noalloc_fail(AR_ERR_UNSUPPORTED_N, "n_samples=%d: supported lengths are 1024, 2048, 4096",
                         ev->n_samples);
   if (static_cast<long long>(ev->n_stations) * ev->n_samples > kNoAllocMaxStationSamples)
     return noalloc_fail(AR_ERR_INVALID_ARG,
                         "n_stations x n_samples = %lld exceeds the fixed scratch of ar_unfold_noalloc "
-                        "(at most %lld, e.g. 488 stations of 2048 samples)",
+                        "(at most %lld: 240 stations of 4096, 480 of 2048 or 960 of 1024 samples)",
                         static_cast<long long>(ev->n_stations) * ev->n_samples, kNoAllocMaxStationSamples);
   if (!ev->traces || !ev->pos_m || !ev->t_start_ns || !ev->dirs_rad ||
       reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0)

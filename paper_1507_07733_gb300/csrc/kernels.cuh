@@ -6,8 +6,9 @@
 //   unfold_kernel            per (station, direction) pair: VEL interpolation (corner slabs of
 //                            the pattern staged by TMA bulk copies), 2x2 solve per bin, inverse
 //                            transform of the one-sided (analytic) spectrum, E-field, envelope,
-//                            peak; a persistent grid walks the pairs station-major
-//   residual_kernel          per direction, FP64 plane-wave timing residual, one warp each
+//                            peak; a persistent grid walks the pairs direction-major; the CTA
+//                            that finishes a direction last computes that direction's FP64
+//                            plane-wave timing residual (per-direction completion counters)
 //
 // Transform layout. The band holds at most M = N/4 bins, k in [k_lo, k_lo + M). The inverse
 // transform z[n] = sum_k Z[k] exp(2 pi i k n / N) is evaluated at n = 4m + r (r = 0..3) as
@@ -107,6 +108,37 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigne
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// hardware approximations (relative error of a few ulp): used where FP32 rounding of the
+// result is far below the path's 1e-5 tolerance
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// read-only load that asks L1 to keep the line (twiddle tables reused by every pair)
+__device__ __forceinline__ float2 ldg_keep(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+// streaming store: the output is written once and not read back by the kernel
+__device__ __forceinline__ void st_stream(float* p, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// programmatic dependent launch: let the next kernel in the stream start its prologue, and
+// wait for the previous kernel's completion (both are no-ops without the launch attribute)
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_prior() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 // ---- K1: forward transform of the station voltages ---------------------------------------
 
@@ -115,7 +147,18 @@ struct SpectrumParams {
   float4* spec;            // [S][M]: (X0[k], X1[k]) for k = k_lo + j
   const float2* twf;       // [Q][P]: exp(-2 pi i p q / M) at [q][p]
   const float2* wn;        // [N]: exp(-2 pi i t / N)
+  unsigned* dir_done;      // [n_dir] per-direction completion counters, zeroed here
+  int n_dir;
   int k_lo;
+};
+
+template <int N_>
+struct SpectrumSmem {
+  using L = Layout<N_>;
+  static constexpr size_t XS = 0;                                           // [4][M] float2
+  static constexpr size_t B = XS + sizeof(float2) * L::N;                   // [4][PLN] float2
+  static constexpr size_t TWF = B + sizeof(float2) * 4 * L::PLN;            // [Q][P] float2
+  static constexpr size_t TOTAL = TWF + sizeof(float2) * L::M;
 };
 
 // Z[k] = sum_r W_N^{kr} U_r[k mod M], U_r = M-point DFT of x[4m + r]; the M-point DFT is
@@ -123,12 +166,15 @@ struct SpectrumParams {
 template <int N_>
 __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(SpectrumParams prm) {
   using L = Layout<N_>;
+  using SM = SpectrumSmem<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* xs = reinterpret_cast<float2*>(smem_raw);   // [4][M]: x[4m + r] at [r][m]; later U_r
-  float2* B = xs + N;                                   // [4][P][LDA] (plane stride PLN)
+  float2* xs = reinterpret_cast<float2*>(smem_raw + SM::XS);   // x[4m + r] at [r][m]; later U_r
+  float2* B = reinterpret_cast<float2*>(smem_raw + SM::B);
+  float2* twf = reinterpret_cast<float2*>(smem_raw + SM::TWF);
   const int s = blockIdx.x;
   const int tid = threadIdx.x;
+  pdl_launch_dependents();
 
   const float4* v0 = reinterpret_cast<const float4*>(prm.traces + static_cast<size_t>(s) * 2 * N);
   const float4* v1 = v0 + N / 4;
@@ -138,6 +184,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
     xs[1 * M + m] = make_float2(a.y, b.y);
     xs[2 * M + m] = make_float2(a.z, b.z);
     xs[3 * M + m] = make_float2(a.w, b.w);
+    twf[m] = __ldg(prm.twf + m);
   }
   __syncthreads();
   // pass 1: task (r, m1), Q-point DFT over m2, twiddle W_M^{m1 k2}
@@ -147,7 +194,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
     static_for<0, Q>([&](auto m2) { x[m2] = xs[r * M + m1 + P * m2]; });
     dft<Q, -1>(x);
     static_for<0, Q>([&](auto k2) {
-      if constexpr (k2 != 0) x[k2] = cmul(x[k2], __ldg(prm.twf + k2 * P + m1));
+      if constexpr (k2 != 0) x[k2] = cmul(x[k2], twf[k2 * P + m1]);
       B[r * PLN + m1 * LDA + k2] = x[k2];
     });
   }
@@ -161,25 +208,31 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
     static_for<0, P>([&](auto k1) { xs[r * M + k2 + Q * k1] = y[k1]; });
   }
   __syncthreads();
+  // the previous kernel in the stream may still read the spectra: wait before writing them
+  pdl_wait_prior();
+  if (s == 0)
+    for (int d = tid; d < prm.n_dir; d += T) prm.dir_done[d] = 0u;
   // combine the four decimated transforms at k and N - k, split the channels
   float4* out = prm.spec + static_cast<size_t>(s) * M;
   for (int j = tid; j < M; j += T) {
     const int k = prm.k_lo + j;
     const int kk = k % M, km = (M - kk) % M;
+    const float2 w1 = __ldg(prm.wn + k);                  // W_N^k; W_N^{2k}, W_N^{3k} by products
+    const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
     float2 z = xs[kk], zm = xs[km];
-#pragma unroll
-    for (int r = 1; r < 4; ++r) {
-      const float2 w = __ldg(prm.wn + (k * r) % N);           // W_N^{kr}
-      z = cadd(z, cmul(xs[r * M + kk], w));
-      zm = cadd(zm, cmulc(xs[r * M + km], w));                // W_N^{-kr} = conj
-    }
+    z = cadd(z, cmul(xs[M + kk], w1));
+    zm = cadd(zm, cmulc(xs[M + km], w1));                 // W_N^{-kr} = conj
+    z = cadd(z, cmul(xs[2 * M + kk], w2));
+    zm = cadd(zm, cmulc(xs[2 * M + km], w2));
+    z = cadd(z, cmul(xs[3 * M + kk], w3));
+    zm = cadd(zm, cmulc(xs[3 * M + km], w3));
     const float2 sum = make_float2(z.x + zm.x, z.y - zm.y);   // Z[k] + conj Z[N-k]
     const float2 dif = make_float2(z.x - zm.x, z.y + zm.y);   // Z[k] - conj Z[N-k]
     out[j] = make_float4(0.5f * sum.x, 0.5f * sum.y, 0.5f * dif.y, -0.5f * dif.x);
   }
 }
 
-// ---- K3: fused per-pair unfold ------------------------------------------------------------
+// ---- K3: fused per-pair unfold + per-direction residual ------------------------------------
 
 struct UnfoldParams {
   const float4* spec;        // [S][M] station spectra in the band window
@@ -188,14 +241,19 @@ struct UnfoldParams {
   const float2* t1;          // [4][Q][P] pass-1 output twiddles
   const double* dirs;        // [D][2]
   const double* t_start;     // [S]
+  const double* pos;         // [S][3]
   float* efield;             // [D][S][2][N] or null
   float* envelope;           // [D][S][N] or null
   int* peak_idx;             // [D][S]
   float* peak_amp;           // [D][S]
   double* peak_time;         // [D][S]
   unsigned* status;          // [D][S]
+  double* residual;          // [D][S]
+  double* t0;                // [D]
+  double* chi2;              // [D]
   unsigned* err;             // device error word
-  double zen0, dzen, az0, daz, dt_ns;
+  unsigned* dir_done;        // [D] pairs finished per direction (zero at launch, reset by its last CTA)
+  double zen0, dzen, az0, daz, dt_ns, n_over_c;
   int n_zen, n_az, n_f;
   int n_st, n_dir, k_lo;
   long long total_pairs;
@@ -243,19 +301,32 @@ __device__ __forceinline__ DirInfo direction_cell(const UnfoldParams& p, double 
   return di;
 }
 
-// Pass 1 for one (pol, r, ja): load E_p[ja + P jb], pre-twiddle exp(2 pi i jb r / 4Q), Q-point
-// inverse DFT, output twiddle T1[r][mb][ja].
-template <int N_, int R>
-__device__ __forceinline__ void pass1_task(const float2* Ep, int ja, const float2* __restrict__ t1,
+// Pre-twiddles of pass 1, exp(2 pi i jb r / 4Q) at [r][jb], for Q = 32 and Q = 16. They are
+// read with a warp-uniform r so that one copy of the pass-1 code serves all four r: the
+// kernel is limited by instruction fetch when the four variants are compiled separately.
+__constant__ float2 c_pre32[4][32];
+__constant__ float2 c_pre16[4][16];
+
+// Pass 1 for one (pol, r, ja): load E_p[ja + P jb], pre-twiddle, Q-point inverse DFT, output
+// twiddle T1[r][mb][ja].
+template <int N_>
+__device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, const float2* __restrict__ t1,
                                            float2 (&x)[Layout<N_>::Q]) {
   using L = Layout<N_>;
   constexpr int Q = L::Q, P = L::P;
+  static_assert(Q == 32 || Q == 16, "pre-twiddle tables exist for Q = 16 and 32");
   static_for<0, Q>([&](auto jb) {
-    x[jb] = twmul<long(decltype(jb)::value) * R, 4 * Q, +1>(Ep[ja + P * jb]);
+    constexpr int JB = decltype(jb)::value;
+    const float2 e = Ep[ja + P * JB];
+    if constexpr (JB == 0) {
+      x[JB] = e;
+    } else {
+      x[JB] = cmul(e, Q == 32 ? c_pre32[r][JB] : c_pre16[r][JB]);
+    }
   });
   dft<Q, +1>(x);
-  const float2* tw = t1 + (R * Q) * P + ja;
-  static_for<0, Q>([&](auto mb) { x[mb] = cmul(x[mb], __ldg(tw + mb * P)); });
+  const float2* tw = t1 + (r * Q) * P + ja;
+  static_for<0, Q>([&](auto mb) { x[mb] = cmul(x[mb], ldg_keep(tw + mb * P)); });
 }
 
 template <int N_>
@@ -266,13 +337,60 @@ struct UnfoldSmem {
   static constexpr size_t PW = A + sizeof(float2) * L::A_F2;
   static constexpr size_t SPEC = PW + ((sizeof(float) * L::PW_F + 15) / 16) * 16;
   static constexpr size_t BINF = SPEC + sizeof(float4) * L::M;
-  static constexpr size_t DIR = BINF + sizeof(int2) * L::M;            // 2 DirInfo
-  static constexpr size_t RED = DIR + 2 * sizeof(DirInfo);             // T/32 (float,int) + flags
-  static constexpr size_t BAR = RED + 16 * (L::T / 32) + 16;
+  static constexpr size_t DIR = BINF + sizeof(int2) * L::M;            // 1 DirInfo
+  static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // T/32 x (double, float, int) + flags
+  static constexpr size_t BAR = RED + 16 * (L::T / 32) + 32;
   static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2
   __host__ __device__ static size_t hn(int n_f) { return SLAB + sizeof(float2) * 16 * n_f; }
-  __host__ __device__ static size_t total(int n_f) { return hn(n_f) + sizeof(float2) * 4 * n_f; }
+  // hn: per frequency node f, the 4 VEL entries at f and their slope to f + 1
+  __host__ __device__ static size_t total(int n_f) { return hn(n_f) + sizeof(float2) * 8 * n_f; }
 };
+
+// Residual of direction d over all stations, by the whole CTA (FP64, deterministic order:
+// station s is handled by thread s mod T, and partial sums are combined in a fixed tree).
+template <int T>
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double t = red[0];
+#pragma unroll
+  for (int i = 1; i < T / 32; ++i) t += red[i];
+  return t;
+}
+
+template <int T>
+__device__ __forceinline__ void direction_residual(const UnfoldParams& p, int d, double* red) {
+  const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
+  const double sz = sin(zen);
+  const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
+  const double* tp = p.peak_time + static_cast<size_t>(d) * p.n_st;
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < p.n_st; s += T) {
+    const double* x = p.pos + 3 * s;
+    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
+    acc = __dadd_rn(acc, __dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c)));   // t_s - tau_s
+  }
+  const double mean = __ddiv_rn(block_sum_fixed<T>(acc, red), static_cast<double>(p.n_st));
+  double ss = 0.0;
+  double* res = p.residual + static_cast<size_t>(d) * p.n_st;
+  for (int s = threadIdx.x; s < p.n_st; s += T) {
+    const double* x = p.pos + 3 * s;
+    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
+    const double r = __dsub_rn(__dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c)), mean);
+    res[s] = r;
+    ss = __fma_rn(r, r, ss);
+  }
+  ss = block_sum_fixed<T>(ss, red);
+  if (threadIdx.x == 0) {
+    p.t0[d] = mean;
+    p.chi2[d] = ss;
+    p.dir_done[d] = 0u;   // ready for the next launch
+  }
+}
 
 template <int N_>
 __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm) {
@@ -288,17 +406,23 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
   float4* sspec = reinterpret_cast<float4*>(smem_raw + SM::SPEC);
   int2* sbinf = reinterpret_cast<int2*>(smem_raw + SM::BINF);
   DirInfo* sdir = reinterpret_cast<DirInfo*>(smem_raw + SM::DIR);
-  float* redv = reinterpret_cast<float*>(smem_raw + SM::RED);
-  int* redi = reinterpret_cast<int*>(redv + T / 32);
+  double* redd = reinterpret_cast<double*>(smem_raw + SM::RED);      // T/32 doubles
+  float* redv = reinterpret_cast<float*>(redd + T / 32);             // T/32 floats
+  int* redi = reinterpret_cast<int*>(redv + T / 32);                 // T/32 ints
+  int* sflag = redi + T / 32;                                        // 1 int
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + SM::BAR);
   float2* slab = reinterpret_cast<float2*>(smem_raw + SM::SLAB);
   float2* hn = reinterpret_cast<float2*>(smem_raw + SM::hn(prm.n_f));
 
   const int tid = threadIdx.x;
   const int n_f = prm.n_f;
+  const int S = prm.n_st;
+  pdl_launch_dependents();   // the next kernel may start its prologue as CTAs retire
   const unsigned slab_bytes = static_cast<unsigned>(n_f) * 4u * sizeof(float2);
+  constexpr unsigned spec_bytes = sizeof(float4) * M;
+  const size_t node = static_cast<size_t>(n_f) * 4;
 
-  // contiguous chunk of the station-major pair space
+  // contiguous chunk of the direction-major pair space (q = d * S + s)
   const long long per = prm.total_pairs / gridDim.x, rem = prm.total_pairs % gridDim.x;
   const long long q0 = blockIdx.x * per + min(static_cast<long long>(blockIdx.x), rem);
   const long long q1 = q0 + per + (blockIdx.x < rem ? 1 : 0);
@@ -307,82 +431,75 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
   for (int j = tid; j < M; j += T) sbinf[j] = __ldg(prm.binf + j);
   if (tid == 0) {
     mbar_init(bar, 1);
-    const int d = static_cast<int>(q0 % prm.n_dir);
-    DirInfo di = direction_cell(prm, prm.dirs[2 * d], prm.dirs[2 * d + 1]);
-    sdir[0] = di;
-    mbar_arrive_expect_tx(bar, 4 * slab_bytes);
-    const float2* base = prm.table;
-    const size_t node = static_cast<size_t>(n_f) * 4;
-    tma_bulk_g2s(slab + 0 * n_f * 4, base + di.slab0 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 1 * n_f * 4, base + di.slab1 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 2 * n_f * 4, base + di.slab2 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 3 * n_f * 4, base + di.slab3 * node, slab_bytes, bar);
+    const int d = static_cast<int>(q0 / S), s = static_cast<int>(q0 % S);
+    const DirInfo di = direction_cell(prm, prm.dirs[2 * d], prm.dirs[2 * d + 1]);
+    *sdir = di;
+    mbar_arrive_expect_tx(bar, 4 * slab_bytes + spec_bytes);
+    tma_bulk_g2s(slab + 0 * node, prm.table + di.slab0 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 1 * node, prm.table + di.slab1 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 2 * node, prm.table + di.slab2 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 3 * node, prm.table + di.slab3 * node, slab_bytes, bar);
+    pdl_wait_prior();   // the station spectra come from the previous kernel
+    tma_bulk_g2s(sspec, prm.spec + static_cast<size_t>(s) * M, spec_bytes, bar);
   }
+  pdl_wait_prior();
   __syncthreads();   // barrier initialised, first direction and frequency cells visible
-  int cur_s = -1;
-  unsigned phase = 0;
 
+  int cur_d = -1;
+  int pairs_in_dir = 0;
+  DirInfo di;
+  unsigned phase = 0;
   for (long long q = q0; q < q1; ++q, phase ^= 1u) {
-    const int s = static_cast<int>(q / prm.n_dir), d = static_cast<int>(q % prm.n_dir);
-    const int buf = static_cast<int>((q - q0) & 1);
-    if (s != cur_s) {   // new station: its band-window spectrum into shared memory
-      const float4* src = prm.spec + static_cast<size_t>(s) * M;
-      for (int j = tid; j < M; j += T) sspec[j] = __ldg(src + j);
-      cur_s = s;
-    }
-    // corner slabs of this pair's direction
+    const int d = static_cast<int>(q / S), s = static_cast<int>(q % S);
     const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(prm.err, kErrTmaTimeout);
       return;
     }
-    const DirInfo di = sdir[buf];
-    // angular (bilinear) interpolation at every frequency node
-    for (int e = tid; e < n_f * 4; e += T) {
-      const float2 a = slab[e], b = slab[n_f * 4 + e], c = slab[2 * n_f * 4 + e], dd = slab[3 * n_f * 4 + e];
-      float2 h;
-      h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
-      h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
-      hn[e] = h;
-    }
-    __syncthreads();   // hn, sspec ready; slab free
-    if (tid == 0 && q + 1 < q1) {   // prefetch the next pair's slabs
-      const int dn = static_cast<int>((q + 1) % prm.n_dir);
-      DirInfo nx = direction_cell(prm, prm.dirs[2 * dn], prm.dirs[2 * dn + 1]);
-      sdir[buf ^ 1] = nx;
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, 4 * slab_bytes);
-      const size_t node = static_cast<size_t>(n_f) * 4;
-      tma_bulk_g2s(slab + 0 * n_f * 4, prm.table + nx.slab0 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 1 * n_f * 4, prm.table + nx.slab1 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 2 * n_f * 4, prm.table + nx.slab2 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 3 * n_f * 4, prm.table + nx.slab3 * node, slab_bytes, bar);
+    if (d != cur_d) {   // new direction: angular (bilinear) interpolation at every frequency node
+      di = *sdir;
+      const auto bilin = [&](int e) {
+        const float2 a = slab[e], b = slab[node + e], c = slab[2 * node + e], dd = slab[3 * node + e];
+        float2 h;
+        h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+        h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+        return h;
+      };
+      for (int e = tid; e < n_f * 4; e += T) {
+        const int f = e >> 2, cp = e & 3;
+        const float2 h = bilin(e);
+        const float2 h1 = f + 1 < n_f ? bilin(e + 4) : h;
+        hn[8 * f + cp] = h;
+        hn[8 * f + 4 + cp] = csub(h1, h);
+      }
+      cur_d = d;
+      __syncthreads();
     }
 
     // ---- frequency interpolation + 2x2 solve per bin ----
     const bool valid = (di.st & kStBadDir) == 0;
     bool sing = false;
     constexpr float kScale = 2.0f / static_cast<float>(N);
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < NB; ++i) {
       const int j = tid + T * i;
       const int2 bf = sbinf[j];
       float2 et = make_float2(0.f, 0.f), ep = et;
       if (bf.x >= 0 && valid) {
         const float tf = __int_as_float(bf.y);
-        const float4* h0 = reinterpret_cast<const float4*>(hn + 4 * bf.x);
-        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
-        const float2 a = make_float2(fmaf(tf, g01.x - h01.x, h01.x), fmaf(tf, g01.y - h01.y, h01.y));   // H0t
-        const float2 b = make_float2(fmaf(tf, g01.z - h01.z, h01.z), fmaf(tf, g01.w - h01.w, h01.w));   // H0p
-        const float2 c = make_float2(fmaf(tf, g23.x - h23.x, h23.x), fmaf(tf, g23.y - h23.y, h23.y));   // H1t
-        const float2 dd = make_float2(fmaf(tf, g23.z - h23.z, h23.z), fmaf(tf, g23.w - h23.w, h23.w));  // H1p
+        const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
+        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];   // value, slope
+        const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));    // H0t
+        const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));    // H0p
+        const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));    // H1t
+        const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));   // H1p
         const float4 V = sspec[j];
         const float2 v0 = make_float2(V.x, V.y), v1 = make_float2(V.z, V.w);
         const float2 det = csub(cmul(a, dd), cmul(b, c));
-        const float sc = sqrtf(cabs2(a) * cabs2(dd)) + sqrtf(cabs2(b) * cabs2(c));
+        const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
         const float dd2 = cabs2(det);
         if (dd2 > 1e-12f * sc * sc) {
-          const float inv = kScale / dd2;
+          const float inv = kScale * rcp_approx(dd2);
           const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
           const float2 np = csub(cmul(a, v1), cmul(c, v0));
           const float2 ct = cmulc(nt, det), cp = cmulc(np, det);
@@ -395,7 +512,25 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       E[j] = et;
       E[M + j] = ep;
     }
-    const bool any_sing = __syncthreads_or(sing);
+    const bool any_sing = __syncthreads_or(sing);   // spectrum and slab buffers free from here
+    if (tid == 0 && q + 1 < q1) {                    // prefetch the next pair's inputs
+      const int dn = static_cast<int>((q + 1) / S), sn = static_cast<int>((q + 1) % S);
+      unsigned bytes = spec_bytes;
+      fence_proxy_async_smem();
+      if (dn != d) {
+        const DirInfo nx = direction_cell(prm, prm.dirs[2 * dn], prm.dirs[2 * dn + 1]);
+        *sdir = nx;
+        bytes += 4 * slab_bytes;
+        mbar_arrive_expect_tx(bar, bytes);
+        tma_bulk_g2s(slab + 0 * node, prm.table + nx.slab0 * node, slab_bytes, bar);
+        tma_bulk_g2s(slab + 1 * node, prm.table + nx.slab1 * node, slab_bytes, bar);
+        tma_bulk_g2s(slab + 2 * node, prm.table + nx.slab2 * node, slab_bytes, bar);
+        tma_bulk_g2s(slab + 3 * node, prm.table + nx.slab3 * node, slab_bytes, bar);
+      } else {
+        mbar_arrive_expect_tx(bar, bytes);
+      }
+      tma_bulk_g2s(sspec, prm.spec + static_cast<size_t>(sn) * M, spec_bytes, bar);
+    }
 
     // ---- pass 1: Q-point DFTs per (pol, r, ja) ----
     {
@@ -404,12 +539,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       const int ja = tid % P;
       float2 x[Q];
       const float2* Ep = E + pol * M;
-      switch (r) {
-        case 0: pass1_task<N_, 0>(Ep, ja, prm.t1, x); break;
-        case 1: pass1_task<N_, 1>(Ep, ja, prm.t1, x); break;
-        case 2: pass1_task<N_, 2>(Ep, ja, prm.t1, x); break;
-        default: pass1_task<N_, 3>(Ep, ja, prm.t1, x); break;
-      }
+      pass1_task<N_>(Ep, ja, r, prm.t1, x);
       __syncthreads();   // every E read done: A may overwrite it
       const int row = (prm.k_lo + ja) % P;
       float2* dst = A + (pol * 4 + r) * PLN + row * LDA;
@@ -418,13 +548,13 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
     __syncthreads();
 
     // ---- pass 2: P-point DFTs, E-field, envelope, peak ----
-    const size_t pair = static_cast<size_t>(d) * prm.n_st + s;
+    const size_t pair = static_cast<size_t>(d) * S + s;
     float bv = -1.0f;
     int bi = 0;
     if constexpr (SPLIT == 1) {
       const int r = tid & 3, mb = tid >> 2;
       float pw[P];
-#pragma unroll
+#pragma unroll 1
       for (int pol = 0; pol < 2; ++pol) {
         float2 y[P];
         const float2* src = A + (pol * 4 + r) * PLN + mb;
@@ -432,14 +562,18 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
         dft<P, +1>(y);
         if (prm.efield) {
           float* ef = prm.efield + (pair * 2 + pol) * N + tid;
-          static_for<0, P>([&](auto ma) { ef[T * ma] = y[ma].x; });
+          static_for<0, P>([&](auto ma) { st_stream(ef + T * ma, y[ma].x); });
         }
-        static_for<0, P>([&](auto ma) { pw[ma] = pol == 0 ? cabs2(y[ma]) : pw[ma] + cabs2(y[ma]); });
+        if (pol == 0) {
+          static_for<0, P>([&](auto ma) { pw[ma] = cabs2(y[ma]); });
+        } else {
+          static_for<0, P>([&](auto ma) { pw[ma] += cabs2(y[ma]); });
+        }
       }
       float* en = prm.envelope ? prm.envelope + pair * N + tid : nullptr;
       static_for<0, P>([&](auto ma) {
-        const float v = sqrtf(pw[ma]);
-        if (en) en[T * ma] = v;
+        const float v = sqrt_approx(pw[ma]);
+        if (en) st_stream(en + T * ma, v);
         if (v > bv) { bv = v; bi = tid + T * ma; }
       });
     } else {
@@ -453,7 +587,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       dft<P, +1>(y);
       if (prm.efield) {
         float* ef = prm.efield + (pair * 2 + pol) * N + tq;
-        static_for<0, P>([&](auto ma) { ef[TQ * ma] = y[ma].x; });
+        static_for<0, P>([&](auto ma) { st_stream(ef + TQ * ma, y[ma].x); });
       }
       float pw[P];
       static_for<0, P>([&](auto ma) {
@@ -465,14 +599,14 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       const float* other = PWX + (1 - pol) * P * TQ + tq;
       if (pol == 0) {
         static_for<0, P / 2>([&](auto ma) {
-          const float v = sqrtf(pw[ma] + other[ma * TQ]);
-          if (en) en[TQ * ma] = v;
+          const float v = sqrt_approx(pw[ma] + other[ma * TQ]);
+          if (en) st_stream(en + TQ * ma, v);
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       } else {
         static_for<P / 2, P>([&](auto ma) {
-          const float v = sqrtf(pw[ma] + other[ma * TQ]);
-          if (en) en[TQ * ma] = v;
+          const float v = sqrt_approx(pw[ma] + other[ma * TQ]);
+          if (en) st_stream(en + TQ * ma, v);
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       }
@@ -486,6 +620,8 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
     }
     if ((tid & 31) == 0) { redv[tid >> 5] = bv; redi[tid >> 5] = bi; }
     __syncthreads();
+    ++pairs_in_dir;
+    const bool dir_end = (q + 1 == q1) || ((q + 1) / S != d);
     if (tid == 0) {
 #pragma unroll
       for (int w = 1; w < T / 32; ++w) {
@@ -496,60 +632,19 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       prm.peak_amp[pair] = bv;
       prm.peak_time[pair] = __dadd_rn(prm.t_start[s], __dmul_rn(static_cast<double>(bi), prm.dt_ns));
       prm.status[pair] = di.st | (any_sing ? kStSingular : 0u);
+      if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
+        __threadfence();
+        const unsigned before = atomicAdd(prm.dir_done + d, static_cast<unsigned>(pairs_in_dir));
+        *sflag = (before + pairs_in_dir == static_cast<unsigned>(S)) ? 1 : 0;
+        __threadfence();
+      }
     }
-    __syncthreads();   // A, redv free for the next pair
-  }
-}
-
-// ---- K4: per-direction plane-wave residual (FP64) ----------------------------------------
-
-struct ResidualParams {
-  const double* pos;        // [S][3]
-  const double* dirs;       // [D][2]
-  const double* peak_time;  // [D][S]
-  double* residual;         // [D][S]
-  double* t0;               // [D]
-  double* chi2;             // [D]
-  double n_over_c;          // n_refr / c  [ns/m]
-  int n_st, n_dir;
-};
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
-
-__global__ void __launch_bounds__(128) residual_kernel(ResidualParams p) {
-  const int d = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (d >= p.n_dir) return;
-  const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
-  const double sz = sin(zen);
-  const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
-  const double* tp = p.peak_time + static_cast<size_t>(d) * p.n_st;
-  double acc = 0.0;
-  for (int s = lane; s < p.n_st; s += 32) {
-    const double* x = p.pos + 3 * s;
-    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    const double tau = -__dmul_rn(dot, p.n_over_c);
-    acc = __dadd_rn(acc, __dsub_rn(tp[s], tau));
-  }
-  const double mean = __ddiv_rn(warp_sum(acc), static_cast<double>(p.n_st));
-  double ss = 0.0;
-  double* res = p.residual + static_cast<size_t>(d) * p.n_st;
-  for (int s = lane; s < p.n_st; s += 32) {
-    const double* x = p.pos + 3 * s;
-    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    const double tau = -__dmul_rn(dot, p.n_over_c);
-    const double r = __dsub_rn(__dsub_rn(tp[s], tau), mean);
-    res[s] = r;
-    ss = __fma_rn(r, r, ss);
-  }
-  ss = warp_sum(ss);
-  if (lane == 0) {
-    p.t0[d] = mean;
-    p.chi2[d] = ss;
+    if (dir_end) {
+      pairs_in_dir = 0;
+      __syncthreads();
+      if (*sflag) direction_residual<T>(prm, d, redd);
+    }
+    __syncthreads();   // A, reductions free for the next pair
   }
 }
 

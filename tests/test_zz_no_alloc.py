@@ -77,7 +77,7 @@ def test_noalloc_refuses_events_beyond_its_scratch():
     from paper_1507_07733_gb300 import binding
     pat = synth.make_pattern()
     table = _dev(pat.table)
-    S, N, D = 245, 4096, 1              # 245 x 4096 > 1,000,000 stations x samples
+    S, N, D = 241, 4096, 1              # 241 x 4096 > 983,040 stations x samples
     tr = torch.zeros((S, 2, N), dtype=torch.float32, device="cuda")
     pos = torch.zeros((S, 3), dtype=torch.float64, device="cuda")
     ts = torch.zeros((S,), dtype=torch.float64, device="cuda")
@@ -85,4 +85,4 @@ def test_noalloc_refuses_events_beyond_its_scratch():
     out, st = binding.alloc_outputs(D, S, N)
     with pytest.raises(binding.ArError) as e:
         binding.ar_unfold_noalloc(pat.desc(), table.data_ptr(), binding.make_event(-1, tr, pos, ts, dirs), st)
-    assert e.value.status == 1 and "1000000" in str(e.value)
+    assert e.value.status == 1 and "983040" in str(e.value)
