@@ -293,6 +293,10 @@ def run_gpu(args):
         e2e = {"value": round(pairs * world * n_e2e / el, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": round(el / n_e2e * 1e3, 4)}
 
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, binding, synth, ctx, pid, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         p_pairs, p_dt, threads = time_oracle(pat, ev, steps=args.cpu_steps, warmup=1)
@@ -317,10 +321,67 @@ def run_gpu(args):
             "kernel_ms": {"station_spectrum": round(k1, 5), "unfold_with_residual": round(k3, 5)},
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,
+            "batched_uneven": batched,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(h0, h1),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_batched(args, binding, synth, ctx, pid, dev, stream):
+    """The 256-event uneven workload: 256 plain ar_unfold calls vs one batch graph launch
+    (autotuned plan), same outputs buffers, device time with CUDA events."""
+    import torch
+    descs = synth.uneven_stream(256)
+    evs = [synth.materialise(d) for d in descs]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    outs = [binding.alloc_outputs(e.n_dirs, e.n_stations, e.n_samples, device=dev)[0] for e in evs]
+    keep = [(t(e.traces), t(e.pos_m), t(e.t_start_ns), t(e.dirs_rad)) for e in evs]   # device inputs
+    structs = [binding.make_event(pid, *k, e.fs_hz) for k, e in zip(keep, evs)]
+    ostructs = [binding.outputs_struct(o) for o in outs]
+    pairs = sum(e.n_stations * e.n_dirs for e in evs)
+    sp = stream.cuda_stream
+    for e in evs:   # tables and workspace for every shape before timing
+        ctx.prepare(e.n_samples, e.fs_hz, pid, max(x.n_stations for x in evs))
+    reps = max(3, min(args.steps // 100, 10))
+
+    def timed(fn, n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n
+
+    def plain():
+        for es, os_ in zip(structs, ostructs):
+            binding.ar_unfold(ctx.h, es, os_, sp)
+
+    plain_ms = timed(plain, reps)
+    bctx = binding.Context(dev.index if dev.index is not None else 0, autotune=True)
+    bpid = bctx.load_pattern(synth.make_pattern())
+    bstructs = [binding.make_event(bpid, *k, e.fs_hz) for k, e in zip(keep, evs)]
+    plan = bctx.batch(256, sum(e.n_stations for e in evs), sum(e.n_dirs for e in evs), 51)
+    plan.run(bstructs, ostructs)      # first run: autotune
+    torch.cuda.synchronize(dev)
+    batch_ms = timed(lambda: plan.run(bstructs, ostructs), reps)
+    ctas, tune_ms = plan.tuning()
+    binding.ar_sync(ctx.h, sp)
+    binding.ar_sync(bctx.h, sp)
+    plan.close()
+    bctx.close()
+    out_bytes = sum(v.numel() * v.element_size() for o in outs for v in o.values() if v is not None)
+    del outs, keep
+    torch.cuda.empty_cache()
+    return {"workload": "256 events: stations U{3..124}, samples {1024, 2048, 4096}, directions U{16..256}",
+            "pairs": pairs, "output_bytes": out_bytes, "reps": reps,
+            "plain_ms": round(plain_ms, 3), "plain_unfolds_per_s": round(pairs / plain_ms * 1e3, 1),
+            "batched_ms": round(batch_ms, 3), "batched_unfolds_per_s": round(pairs / batch_ms * 1e3, 1),
+            "speedup": round(plain_ms / batch_ms, 3), "batched_GBps": round(out_bytes / batch_ms / 1e6, 1),
+            "ctas_per_sm": list(ctas), "autotune_graph_ms": [round(x, 3) for x in tune_ms]}
 
 
 # ---- the reference arm (the oracle, on the host cores) ---------------------------------
@@ -358,6 +419,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40, help="oracle sample steps for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-event batched-vs-plain comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

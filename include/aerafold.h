@@ -171,6 +171,47 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
 ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable);
 ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
 
+/* ---- batched launches over uneven events ----
+ *
+ * A batch plan runs many events of different sizes (stations, trace lengths, direction
+ * counts) in one CUDA-graph launch: per trace length, one station kernel over all stations
+ * and one persistent unfold kernel over all (station, direction) pairs of those events, with
+ * the same per-pair arithmetic as ar_unfold (results are identical bit for bit). */
+typedef struct ar_batch ar_batch;
+
+typedef struct ar_batch_limits {
+  int32_t max_events;    /* events per ar_batch_run (<= 65536)                               */
+  int32_t max_stations;  /* stations summed over the events of one run                       */
+  int32_t max_dirs;      /* directions summed over the events of one run                     */
+  int32_t max_n_freq;    /* largest frequency-node count of the patterns used (2..256)       */
+} ar_batch_limits;
+
+/* Create a plan on ctx: allocates its device workspace (station spectra for max_stations
+ * traces of up to 4096 samples, direction counters, descriptor tables), two pinned staging
+ * buffers, and captures two CUDA graph instances. Synchronous.
+ * Errors: AR_ERR_INVALID_ARG, AR_ERR_OUT_OF_MEMORY, AR_ERR_CUDA. */
+ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* limits, ar_batch** plan);
+
+/* Run n_events events (arrays on the host; each event's and output's arrays are DEVICE
+ * pointers as for ar_unfold) as one graph launch on stream. Asynchronous: returns once the
+ * launch is queued. Two runs may be in flight; a third waits on the host for the first to
+ * finish with its staging buffer. If the context was created with autotune = 1, the first
+ * run times the unfold kernels at 1..4 CTAs per SM (running the batch several times; the
+ * results are the same each time) and keeps the fastest. Device errors are reported by
+ * ar_sync on the plan's context.
+ * Errors: AR_ERR_INVALID_ARG, AR_ERR_UNSUPPORTED_N, AR_ERR_NO_PATTERN, AR_ERR_BUDGET (the
+ * events exceed the plan's limits), AR_ERR_CUDA. */
+ar_status ar_batch_run(ar_batch* plan, const ar_event* events, const ar_outputs* outs, int32_t n_events,
+                       void* stream);
+
+/* Chosen unfold CTAs per SM for the 1024-, 2048- and 4096-sample classes (ctas_per_sm[3]),
+ * and the autotuner's measured graph time in ms for 1..4 CTAs per SM (candidate_ms[4], 0 if
+ * not tried; may be NULL). */
+ar_status ar_batch_tuning(const ar_batch* plan, int32_t* ctas_per_sm, float* candidate_ms);
+
+/* Wait for the plan's runs in flight and free it. NULL is a no-op. */
+ar_status ar_batch_destroy(ar_batch* plan);
+
 /* ar_unfold without any device allocation, for callers that cannot call cudaMalloc: a
  * real-time acquisition loop whose device memory map is fixed after start-up, or a plug-in
  * running inside another program's CUDA context and memory pool. The paper has no

@@ -30,7 +30,7 @@ AR_STATUS_BAD_DIR = 4
 #: every symbol include/aerafold.h declares
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
-            "ar_unfold_noalloc"]
+            "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy"]
 
 
 class LibraryMissing(RuntimeError):
@@ -60,6 +60,11 @@ class ar_event(ctypes.Structure):
                 ("pattern_id", ctypes.c_int32), ("fs_hz", ctypes.c_double),
                 ("refractive_index", ctypes.c_double), ("traces", ctypes.c_void_p),
                 ("pos_m", ctypes.c_void_p), ("t_start_ns", ctypes.c_void_p), ("dirs_rad", ctypes.c_void_p)]
+
+
+class ar_batch_limits(ctypes.Structure):
+    _fields_ = [("max_events", ctypes.c_int32), ("max_stations", ctypes.c_int32), ("max_dirs", ctypes.c_int32),
+                ("max_n_freq", ctypes.c_int32)]
 
 
 class ar_outputs(ctypes.Structure):
@@ -97,6 +102,10 @@ def load(path: str | None = None):
         L.ar_unfold_host.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
         L.ar_set_profiling.argtypes = [vp, i32]
         L.ar_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.ar_batch_create.argtypes = [vp, ctypes.POINTER(ar_batch_limits), ctypes.POINTER(vp)]
+        L.ar_batch_run.argtypes = [vp, vp, vp, i32, vp]
+        L.ar_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+        L.ar_batch_destroy.argtypes = [vp]
         L.ar_unfold_noalloc.argtypes = [ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(ar_event),
                                         ctypes.POINTER(ar_outputs), vp]
         for name in EXPORTED:
@@ -176,6 +185,36 @@ def ar_unfold_noalloc(desc: dict, device_table_ptr: int, ev: ar_event, out: ar_o
     d = ar_pattern_desc(**desc)
     _check(None, load().ar_unfold_noalloc(ctypes.byref(d), ctypes.c_void_p(device_table_ptr), ctypes.byref(ev),
                                           ctypes.byref(out), ctypes.c_void_p(stream)))
+
+
+def ar_batch_create(ctx, max_events: int, max_stations: int, max_dirs: int, max_n_freq: int = 64):
+    h = ctypes.c_void_p()
+    lim = ar_batch_limits(max_events, max_stations, max_dirs, max_n_freq)
+    _check(ctx, load().ar_batch_create(ctx, ctypes.byref(lim), ctypes.byref(h)))
+    return h
+
+
+def ar_batch_run(ctx, plan, events, outs, stream: int = 0) -> None:
+    """``events``/``outs``: sequences of ``ar_event`` / ``ar_outputs`` (device pointers)."""
+    n = len(events)
+    ev_arr = (ar_event * n)(*events)
+    out_arr = (ar_outputs * n)(*outs)
+    _check(ctx, load().ar_batch_run(plan, ctypes.cast(ev_arr, ctypes.c_void_p), ctypes.cast(out_arr, ctypes.c_void_p),
+                                    n, ctypes.c_void_p(stream)))
+
+
+def ar_batch_tuning(plan):
+    """(CTAs per SM for the 1024/2048/4096 classes, autotuner graph ms for 1..4 CTAs per SM)."""
+    c = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_float * 4)()
+    st = load().ar_batch_tuning(plan, c, ms)
+    if st != AR_OK:
+        raise ArError(st, "ar_batch_tuning")
+    return tuple(c), tuple(ms)
+
+
+def ar_batch_destroy(plan) -> None:
+    load().ar_batch_destroy(plan)
 
 
 # ---- PyTorch-facing helpers ----------------------------------------------------------
@@ -260,6 +299,9 @@ class Context:
             ar_sync(self.h, st.cuda_stream)
         return out
 
+    def batch(self, max_events: int, max_stations: int, max_dirs: int, max_n_freq: int = 64) -> "Batch":
+        return Batch(self, max_events, max_stations, max_dirs, max_n_freq)
+
     def sync(self, stream=None) -> None:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
@@ -278,3 +320,32 @@ class Context:
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         ar_unfold_host(self.h, ev, outputs_struct(out), st.cuda_stream)
         return out
+
+
+class Batch:
+    """A batch plan (ar_batch_*) bound to a Context."""
+
+    def __init__(self, ctx: Context, max_events: int, max_stations: int, max_dirs: int, max_n_freq: int = 64):
+        self.ctx = ctx
+        self.h = ar_batch_create(ctx.h, max_events, max_stations, max_dirs, max_n_freq)
+
+    def run(self, events, outs, stream=None) -> None:
+        """events: list of ``ar_event``; outs: list of output dicts (tensors) or ``ar_outputs``."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(self.ctx.device)
+        structs = [o if isinstance(o, ar_outputs) else outputs_struct(o) for o in outs]
+        ar_batch_run(self.ctx.h, self.h, events, structs, st.cuda_stream)
+
+    def tuning(self):
+        return ar_batch_tuning(self.h)
+
+    def close(self):
+        if self.h:
+            ar_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

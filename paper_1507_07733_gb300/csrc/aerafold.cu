@@ -312,53 +312,68 @@ struct PathBuffers {      // library-side buffers one launch of the path uses
   const int2* binf;
 };
 
+// the kernels' view of one event (see EventDesc)
+EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float2* table, const ar_event* ev,
+                    const ar_outputs* out, int k_lo) {
+  EventDesc d{};
+  d.traces = ev->traces;
+  d.pos = ev->pos_m;
+  d.t_start = ev->t_start_ns;
+  d.dirs = ev->dirs_rad;
+  d.efield = out->efield;
+  d.envelope = out->envelope;
+  d.peak_idx = out->peak_idx;
+  d.peak_amp = out->peak_amp;
+  d.peak_time = out->peak_time_ns;
+  d.status = out->status;
+  d.residual = out->residual_ns;
+  d.t0 = out->t0_ns;
+  d.chi2 = out->chi2;
+  d.spec = b.spec;
+  d.dir_done = b.dir_done;
+  d.table = table;
+  d.binf = b.binf;
+  d.t1 = b.t1;
+  d.twf = b.twf;
+  d.wn = b.wn;
+  d.zen0 = pd.zen0_rad;
+  d.dzen = pd.dzen_rad;
+  d.az0 = pd.az0_rad;
+  d.daz = pd.daz_rad;
+  d.dt_ns = 1e9 / ev->fs_hz;
+  d.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  d.pair_begin = 0;
+  d.station_begin = 0;
+  d.n_zen = pd.n_zen;
+  d.n_az = pd.n_az;
+  d.n_f = pd.n_freq;
+  d.n_st = ev->n_stations;
+  d.n_dir = ev->n_dirs;
+  d.k_lo = k_lo;
+  return d;
+}
+
+// one event: the station kernel (one CTA per station), then the persistent unfold kernel
 template <int N_>
 cudaError_t launch_path(const PathBuffers& b, const ar_pattern_desc& pd, const float2* table, const ar_event* ev,
                         const ar_outputs* out, int k_lo, int grid_cap, cudaStream_t stream,
                         cudaEvent_t* evs /* 3 events or null */) {
   using L = Layout<N_>;
-  SpectrumParams sp{ev->traces, b.spec, b.twf, b.wn, b.dir_done, ev->n_dirs, k_lo};
+  PathParams pp{};
+  pp.batch = nullptr;
+  pp.err = b.err;
+  pp.wait_prior = 1;
+  pp.ev0 = make_desc(b, pd, table, ev, out, k_lo);
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, ev->n_stations, L::T, SpectrumSmem<N_>::TOTAL, stream, sp)) !=
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, ev->n_stations, L::T, SpectrumSmem<N_>::TOTAL, stream, pp)) !=
       cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
-  UnfoldParams up{};
-  up.spec = b.spec;
-  up.table = table;
-  up.binf = b.binf;
-  up.t1 = b.t1;
-  up.dirs = ev->dirs_rad;
-  up.t_start = ev->t_start_ns;
-  up.pos = ev->pos_m;
-  up.efield = out->efield;
-  up.envelope = out->envelope;
-  up.peak_idx = out->peak_idx;
-  up.peak_amp = out->peak_amp;
-  up.peak_time = out->peak_time_ns;
-  up.status = out->status;
-  up.residual = out->residual_ns;
-  up.t0 = out->t0_ns;
-  up.chi2 = out->chi2;
-  up.err = b.err;
-  up.dir_done = b.dir_done;
-  up.zen0 = pd.zen0_rad;
-  up.dzen = pd.dzen_rad;
-  up.az0 = pd.az0_rad;
-  up.daz = pd.daz_rad;
-  up.dt_ns = 1e9 / ev->fs_hz;
-  up.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
-  up.n_zen = pd.n_zen;
-  up.n_az = pd.n_az;
-  up.n_f = pd.n_freq;
-  up.n_st = ev->n_stations;
-  up.n_dir = ev->n_dirs;
-  up.k_lo = k_lo;
-  up.total_pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
-  const long long grid = std::min<long long>(grid_cap, up.total_pairs);
+  const long long pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
+  const long long grid = std::min<long long>(grid_cap, pairs);
   if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T, UnfoldSmem<N_>::total(pd.n_freq), stream,
-                      up)) != cudaSuccess)
+                      pp)) != cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[2], stream)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -607,6 +622,306 @@ ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
   AR_CUDA(ctx, cudaEventElapsedTime(&ms[0], ctx->ev[0], ctx->ev[1]));
   AR_CUDA(ctx, cudaEventElapsedTime(&ms[1], ctx->ev[1], ctx->ev[2]));
   ms[2] = 0.0f;   // the residual runs inside the unfold kernel
+  return AR_OK;
+}
+
+}  // extern "C"
+
+// ---- batched launches over uneven events ---------------------------------------------------
+//
+// A plan groups the events of a launch by trace length. Per length class it holds a device
+// copy of the events' descriptors (behind a BatchHeader), and one CUDA graph runs, per class,
+// the copy of the descriptors from pinned host staging, the station kernel (grid-stride over
+// all stations of the class) and the persistent unfold kernel (contiguous chunks of all pairs
+// of the class, crossing event boundaries). Classes are chained with programmatic dependent
+// launch, so the next class's kernels start on SMs as the previous class's CTAs retire. Two
+// pinned staging buffers and two graph instances alternate, so the host can fill the next
+// launch while the previous one runs.
+
+namespace {
+
+constexpr int kClasses = 3;
+int class_of(int n) { return n == 1024 ? 0 : n == 2048 ? 1 : 2; }
+
+}  // namespace
+
+struct ar_batch {
+  ar_ctx* ctx = nullptr;
+  ar_batch_limits lim{};
+  size_t desc_bytes = 0;                       // header + max_events descriptors
+  unsigned char* d_desc[kClasses] = {};        // device descriptors per class
+  unsigned char* h_stage[2][kClasses] = {};    // pinned staging, two sets
+  float4* spec = nullptr;                      // station spectra of all events
+  size_t spec_bytes = 0;
+  unsigned* dir_done = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool pending[2] = {false, false};
+  int next = 0;
+  int ctas_per_sm[kClasses] = {0, 0, 0};       // chosen unfold occupancy per class
+  int max_ctas_per_sm[kClasses] = {0, 0, 0};
+  bool tuned = false;
+  float tune_ms[5] = {0, 0, 0, 0, 0};          // graph time per candidate (autotune)
+};
+
+namespace {
+
+template <int N_>
+PathParams batch_params(ar_batch* b, int c, int wait_prior) {
+  PathParams pp{};
+  pp.batch = reinterpret_cast<const BatchHeader*>(b->d_desc[c]);
+  pp.err = b->ctx->d_err;
+  pp.wait_prior = wait_prior;
+  return pp;
+}
+
+// Each station kernel computes while the previous one runs but waits for it before writing
+// its spectra, so the completion of the last one implies the completion of all of them.
+template <int N_>
+cudaError_t batch_station_launch(ar_batch* b, int c, cudaStream_t st) {
+  using L = Layout<N_>;
+  return launch_pdl(station_spectrum_kernel<N_>, std::min(b->lim.max_stations, 4 * b->ctx->num_sms), L::T,
+                    SpectrumSmem<N_>::TOTAL, st, batch_params<N_>(b, c, 1));
+}
+
+// The first unfold kernel waits for the last station kernel (so for all of them); the later
+// ones need not wait: the kernel before them launches its dependents only after its own wait.
+template <int N_>
+cudaError_t batch_unfold_launch(ar_batch* b, int c, int ctas_per_sm, int wait_prior, cudaStream_t st) {
+  using L = Layout<N_>;
+  return launch_pdl(unfold_kernel<N_>, ctas_per_sm * b->ctx->num_sms, L::T,
+                    UnfoldSmem<N_>::total(b->lim.max_n_freq), st, batch_params<N_>(b, c, wait_prior));
+}
+
+// capture the whole launch (descriptor copies, then per class the two kernels) into graph g
+ar_status batch_build_graph(ar_batch* b, int set, const int* ctas, cudaGraphExec_t* out) {
+  ar_ctx* ctx = b->ctx;
+  cudaStream_t cs;
+  AR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  for (int c = 0; c < kClasses && e == cudaSuccess; ++c)
+    e = cudaMemcpyAsync(b->d_desc[c], b->h_stage[set][c], b->desc_bytes, cudaMemcpyHostToDevice, cs);
+  // station kernels of every class, then the unfold kernels, longest traces first so that
+  // the finest-grained work fills the last tail
+  if (e == cudaSuccess) e = batch_station_launch<1024>(b, 0, cs);
+  if (e == cudaSuccess) e = batch_station_launch<2048>(b, 1, cs);
+  if (e == cudaSuccess) e = batch_station_launch<4096>(b, 2, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<4096>(b, 2, ctas[2], 1, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<2048>(b, 1, ctas[1], 0, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<1024>(b, 0, ctas[0], 0, cs);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  return AR_OK;
+}
+
+// fill staging set `set` with the descriptors of the events
+ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outputs* outs, int n) {
+  ar_ctx* ctx = b->ctx;
+  BatchHeader* hdr[kClasses];
+  EventDesc* dsc[kClasses];
+  for (int c = 0; c < kClasses; ++c) {
+    hdr[c] = reinterpret_cast<BatchHeader*>(b->h_stage[set][c]);
+    dsc[c] = const_cast<EventDesc*>(batch_events(hdr[c]));
+    hdr[c]->n_events = 0;
+    hdr[c]->total_stations = 0;
+    hdr[c]->total_pairs = 0;
+  }
+  size_t spec_off = 0, dir_off = 0;
+  long long stations = 0, dirs = 0;
+  for (int i = 0; i < n; ++i) {
+    const ar_event* ev = &events[i];
+    ar_status st = check_event(ctx, ev, &outs[i]);
+    if (st != AR_OK) return fail(ctx, st, "event %d: %s", i, ctx->last_error.c_str());
+    Resolved rs;
+    if ((st = validate_shape(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, &rs.k_lo)) != AR_OK)
+      return fail(ctx, st, "event %d: %s", i, ctx->last_error.c_str());
+    if (ctx->patterns[ev->pattern_id].desc.n_freq > b->lim.max_n_freq)
+      return fail(ctx, AR_ERR_INVALID_ARG, "event %d: pattern has %d frequency nodes, plan allows %d", i,
+                  ctx->patterns[ev->pattern_id].desc.n_freq, b->lim.max_n_freq);
+    if ((st = get_len_tables(ctx, ev->n_samples, rs.k_lo, &rs.lt)) != AR_OK) return st;
+    if ((st = get_bin_table(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, rs.k_lo, &rs.binf)) != AR_OK) return st;
+    stations += ev->n_stations;
+    dirs += ev->n_dirs;
+    const size_t sb = sizeof(float4) * static_cast<size_t>(ev->n_samples / 4) * ev->n_stations;
+    if (stations > b->lim.max_stations || dirs > b->lim.max_dirs || spec_off + sb > b->spec_bytes)
+      return fail(ctx, AR_ERR_BUDGET, "events exceed the plan (stations %lld/%d, directions %lld/%d)", stations,
+                  b->lim.max_stations, dirs, b->lim.max_dirs);
+    const int c = class_of(ev->n_samples);
+    PathBuffers pb{reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(b->spec) + spec_off),
+                   b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+    const PatternDev& pat = ctx->patterns[ev->pattern_id];
+    EventDesc d = make_desc(pb, pat.desc, pat.table, ev, &outs[i], rs.k_lo);
+    d.pair_begin = hdr[c]->total_pairs;
+    d.station_begin = hdr[c]->total_stations;
+    dsc[c][hdr[c]->n_events++] = d;
+    hdr[c]->total_stations += ev->n_stations;
+    hdr[c]->total_pairs += static_cast<long long>(ev->n_stations) * ev->n_dirs;
+    spec_off += (sb + 255) / 256 * 256;
+    dir_off += ev->n_dirs;
+  }
+  return AR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** out) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (!lim || !out) return fail(ctx, AR_ERR_INVALID_ARG, "limits and output must not be NULL");
+  if (lim->max_events < 1 || lim->max_events > (1 << 16) || lim->max_stations < 1 || lim->max_dirs < 1 ||
+      lim->max_n_freq < 2 || lim->max_n_freq > kMaxFreqNodes)
+    return fail(ctx, AR_ERR_INVALID_ARG, "batch limits out of range");
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  ar_batch* b = new ar_batch;
+  b->ctx = ctx;
+  b->lim = *lim;
+  b->desc_bytes = 16 + sizeof(EventDesc) * static_cast<size_t>(lim->max_events);
+  b->spec_bytes = sizeof(float4) * 1024 * static_cast<size_t>(lim->max_stations) +
+                  256 * static_cast<size_t>(lim->max_events);
+  auto cleanup = [&](ar_status st) {
+    ar_batch_destroy(b);
+    return st;
+  };
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+    e = cudaMalloc(&b->d_desc[c], b->desc_bytes);
+    for (int set = 0; set < 2 && e == cudaSuccess; ++set) e = cudaMallocHost(&b->h_stage[set][c], b->desc_bytes);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->spec, b->spec_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dir_done, sizeof(unsigned) * lim->max_dirs);
+  if (e == cudaSuccess) e = cudaMemset(b->dir_done, 0, sizeof(unsigned) * lim->max_dirs);
+  for (int set = 0; set < 2 && e == cudaSuccess; ++set) e = cudaEventCreateWithFlags(&b->done[set], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(fail(ctx, AR_ERR_OUT_OF_MEMORY, "batch allocation failed: %s", cudaGetErrorString(e)));
+  for (int c = 0; c < kClasses; ++c) {
+    for (int set = 0; set < 2; ++set) std::memset(b->h_stage[set][c], 0, b->desc_bytes);
+    const void* fn = c == 0 ? reinterpret_cast<const void*>(unfold_kernel<1024>)
+                     : c == 1 ? reinterpret_cast<const void*>(unfold_kernel<2048>)
+                              : reinterpret_cast<const void*>(unfold_kernel<4096>);
+    const int threads = c == 0 ? Layout<1024>::T : c == 1 ? Layout<2048>::T : Layout<4096>::T;
+    const size_t smem = c == 0 ? UnfoldSmem<1024>::total(lim->max_n_freq)
+                        : c == 1 ? UnfoldSmem<2048>::total(lim->max_n_freq)
+                                 : UnfoldSmem<4096>::total(lim->max_n_freq);
+    const size_t sp_smem = c == 0 ? SpectrumSmem<1024>::TOTAL : c == 1 ? SpectrumSmem<2048>::TOTAL : SpectrumSmem<4096>::TOTAL;
+    const void* sfn = c == 0 ? reinterpret_cast<const void*>(station_spectrum_kernel<1024>)
+                      : c == 1 ? reinterpret_cast<const void*>(station_spectrum_kernel<2048>)
+                               : reinterpret_cast<const void*>(station_spectrum_kernel<4096>);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp_smem))) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas_per_sm[c], fn, threads, smem)) != cudaSuccess)
+      return cleanup(fail(ctx, AR_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e)));
+    if (b->max_ctas_per_sm[c] < 1) return cleanup(fail(ctx, AR_ERR_CUDA, "unfold kernel does not fit an SM"));
+    b->ctas_per_sm[c] = b->max_ctas_per_sm[c];
+  }
+  for (int set = 0; set < 2; ++set) {
+    ar_status st = batch_build_graph(b, set, b->ctas_per_sm, &b->exec[set]);
+    if (st != AR_OK) return cleanup(st);
+  }
+  b->tuned = !ctx->cfg.autotune;
+  *out = b;
+  return AR_OK;
+}
+
+ar_status ar_batch_destroy(ar_batch* b) {
+  if (!b) return AR_OK;
+  cudaSetDevice(b->ctx->device);
+  for (int set = 0; set < 2; ++set) {
+    if (b->pending[set]) cudaEventSynchronize(b->done[set]);
+    if (b->exec[set]) cudaGraphExecDestroy(b->exec[set]);
+    if (b->done[set]) cudaEventDestroy(b->done[set]);
+  }
+  for (int c = 0; c < kClasses; ++c) {
+    cudaFree(b->d_desc[c]);
+    for (int set = 0; set < 2; ++set) cudaFreeHost(b->h_stage[set][c]);
+  }
+  cudaFree(b->spec);
+  cudaFree(b->dir_done);
+  delete b;
+  return AR_OK;
+}
+
+// Autotune: time the whole graph for each unfold occupancy 1..max CTAs per SM (clamped per
+// class) on the current staging set, keep the fastest, rebuild both graphs with it.
+static ar_status batch_autotune(ar_batch* b, int set, cudaStream_t stream) {
+  ar_ctx* ctx = b->ctx;
+  int best_k = 0;
+  float best_ms = 0.f;
+  cudaEvent_t t0, t1;
+  AR_CUDA(ctx, cudaEventCreate(&t0));
+  AR_CUDA(ctx, cudaEventCreate(&t1));
+  const int kmax = std::max(b->max_ctas_per_sm[0], std::max(b->max_ctas_per_sm[1], b->max_ctas_per_sm[2]));
+  for (int k = 1; k <= kmax && k <= 4; ++k) {
+    int ctas[kClasses];
+    for (int c = 0; c < kClasses; ++c) ctas[c] = std::min(k, b->max_ctas_per_sm[c]);
+    cudaGraphExec_t g = nullptr;
+    ar_status st = batch_build_graph(b, set, ctas, &g);
+    if (st != AR_OK) return st;
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      AR_CUDA(ctx, cudaEventRecord(t0, stream));
+      AR_CUDA(ctx, cudaGraphLaunch(g, stream));
+      AR_CUDA(ctx, cudaEventRecord(t1, stream));
+      AR_CUDA(ctx, cudaEventSynchronize(t1));
+      float ms = 0.f;
+      AR_CUDA(ctx, cudaEventElapsedTime(&ms, t0, t1));
+      if (rep > 0) ms_sum += ms;
+    }
+    cudaGraphExecDestroy(g);
+    b->tune_ms[k] = ms_sum / 3.f;
+    if (best_k == 0 || b->tune_ms[k] < best_ms) {
+      best_k = k;
+      best_ms = b->tune_ms[k];
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  for (int c = 0; c < kClasses; ++c) b->ctas_per_sm[c] = std::min(best_k, b->max_ctas_per_sm[c]);
+  for (int s2 = 0; s2 < 2; ++s2) {
+    if (b->pending[s2]) AR_CUDA(ctx, cudaEventSynchronize(b->done[s2]));
+    b->pending[s2] = false;
+    cudaGraphExecDestroy(b->exec[s2]);
+    b->exec[s2] = nullptr;
+    ar_status st = batch_build_graph(b, s2, b->ctas_per_sm, &b->exec[s2]);
+    if (st != AR_OK) return st;
+  }
+  b->tuned = true;
+  return AR_OK;
+}
+
+ar_status ar_batch_run(ar_batch* b, const ar_event* events, const ar_outputs* outs, int32_t n_events,
+                       void* stream) {
+  if (!b) return AR_ERR_INVALID_ARG;
+  ar_ctx* ctx = b->ctx;
+  if (!events || !outs || n_events < 1) return fail(ctx, AR_ERR_INVALID_ARG, "events and outputs must not be empty");
+  if (n_events > b->lim.max_events)
+    return fail(ctx, AR_ERR_BUDGET, "%d events exceed the plan's %d", n_events, b->lim.max_events);
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int set = b->next;
+  if (b->pending[set]) AR_CUDA(ctx, cudaEventSynchronize(b->done[set]));   // its staging is free again
+  b->pending[set] = false;
+  ar_status st = batch_fill(b, set, events, outs, n_events);
+  if (st != AR_OK) return st;
+  if (!b->tuned) {
+    if ((st = batch_autotune(b, set, s)) != AR_OK) return st;
+  }
+  AR_CUDA(ctx, cudaGraphLaunch(b->exec[set], s));
+  AR_CUDA(ctx, cudaEventRecord(b->done[set], s));
+  b->pending[set] = true;
+  b->next = set ^ 1;
+  return AR_OK;
+}
+
+ar_status ar_batch_tuning(const ar_batch* b, int32_t* ctas_per_sm, float* candidate_ms) {
+  if (!b || !ctas_per_sm) return AR_ERR_INVALID_ARG;
+  for (int c = 0; c < kClasses; ++c) ctas_per_sm[c] = b->ctas_per_sm[c];
+  if (candidate_ms)
+    for (int k = 0; k < 4; ++k) candidate_ms[k] = b->tune_ms[k + 1];
   return AR_OK;
 }
 

@@ -56,9 +56,11 @@ struct Layout : Shape<N_> {
   static constexpr int PLN0 = S::P * LDA;
   static constexpr int PLN = PLN0 + ((4 - PLN0 % 16) + 16) % 16;   // plane stride, == 4 mod 16
   static constexpr int A_F2 = 8 * PLN;                // A: [pol][r][row][mb]; E aliases it
-  static constexpr int PW_F = SPLIT == 2 ? 2 * S::M : 0;   // |Y|^2 exchange between pol threads
   static_assert(SPLIT == 1 || SPLIT == 2, "layout");
   static_assert(A_F2 >= 2 * S::M, "E must fit in A");
+  // with SPLIT == 2, the |Y|^2 exchange between the two polarisations' threads, P x 4Q
+  // floats, also reuses A once pass 2 has read it
+  static_assert(2 * A_F2 >= S::P * 4 * S::Q, "the exchange must fit in A");
   static_assert(T % 32 == 0 && S::M % T == 0, "layout");
 };
 
@@ -140,17 +142,78 @@ __device__ __forceinline__ void pdl_wait_prior() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// ---- K1: forward transform of the station voltages ---------------------------------------
+// ---- events as the kernels see them ------------------------------------------------------
 
-struct SpectrumParams {
+// One event. A plain call passes it inline in the kernel parameters; a batch launch reads
+// an array of them, behind a header, from device memory (so a captured graph can be
+// replayed with new events after a copy into that memory).
+struct EventDesc {
   const float* traces;     // [S][2][N]
-  float4* spec;            // [S][M]: (X0[k], X1[k]) for k = k_lo + j
-  const float2* twf;       // [Q][P]: exp(-2 pi i p q / M) at [q][p]
-  const float2* wn;        // [N]: exp(-2 pi i t / N)
-  unsigned* dir_done;      // [n_dir] per-direction completion counters, zeroed here
-  int n_dir;
-  int k_lo;
+  const double* pos;       // [S][3]
+  const double* t_start;   // [S]
+  const double* dirs;      // [D][2]
+  float* efield;           // [D][S][2][N] or null
+  float* envelope;         // [D][S][N] or null
+  int* peak_idx;           // [D][S]
+  float* peak_amp;         // [D][S]
+  double* peak_time;       // [D][S]
+  unsigned* status;        // [D][S]
+  double* residual;        // [D][S]
+  double* t0;              // [D]
+  double* chi2;            // [D]
+  float4* spec;            // [S][M] station band spectra (library workspace)
+  unsigned* dir_done;      // [D] pairs finished per direction (library workspace)
+  const float2* table;     // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
+  const int2* binf;        // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
+  const float2* t1;        // [4][Q][P] pass-1 output twiddles
+  const float2* twf;       // [Q][P] forward pass twiddles exp(-2 pi i p q / M) at [q][p]
+  const float2* wn;        // [N] exp(-2 pi i t / N)
+  double zen0, dzen, az0, daz, dt_ns, n_over_c;
+  long long pair_begin;    // first pair of the event in the launch's flattened pair space
+  int station_begin;       // first station of the event in the launch's flattened station space
+  int n_zen, n_az, n_f, n_st, n_dir, k_lo;
+  int pad;
 };
+
+struct BatchHeader {       // in device memory, followed by EventDesc[n_events] (16-byte aligned)
+  int n_events;
+  int total_stations;
+  long long total_pairs;
+};
+
+__host__ __device__ inline const EventDesc* batch_events(const BatchHeader* h) {
+  return reinterpret_cast<const EventDesc*>(reinterpret_cast<const unsigned char*>(h) + 16);
+}
+
+struct PathParams {
+  const BatchHeader* batch;   // device batch, or null: the single event ev0
+  unsigned* err;              // device error word
+  int wait_prior;             // wait for the previous kernel in the stream (its results are needed)
+  int pad;
+  EventDesc ev0;
+};
+
+// index of the event whose [begin, begin + count) range holds x (events sorted by begin)
+template <typename F>
+__device__ __forceinline__ int find_event(int n, long long x, F begin_of) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin_of(mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// copy an event descriptor word by word (whole CTA)
+__device__ __forceinline__ void copy_event(EventDesc* dst, const EventDesc* src, int tid, int nthreads) {
+  static_assert(sizeof(EventDesc) % 8 == 0, "descriptor size");
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+  for (int i = tid; i < static_cast<int>(sizeof(EventDesc) / 8); i += nthreads) d[i] = s[i];
+}
+
+
+// ---- K1: forward transform of the station voltages ---------------------------------------
 
 template <int N_>
 struct SpectrumSmem {
@@ -161,10 +224,10 @@ struct SpectrumSmem {
   static constexpr size_t TOTAL = TWF + sizeof(float2) * L::M;
 };
 
-// Z[k] = sum_r W_N^{kr} U_r[k mod M], U_r = M-point DFT of x[4m + r]; the M-point DFT is
-// M = P * Q: input m = m1 + P m2, output k' = k2 + Q k1.
+// One CTA per station of the launch. Z[k] = sum_r W_N^{kr} U_r[k mod M], U_r = M-point DFT of
+// x[4m + r]; the M-point DFT is M = P * Q: input m = m1 + P m2, output k' = k2 + Q k1.
 template <int N_>
-__global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(SpectrumParams prm) {
+__global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(const __grid_constant__ PathParams prm) {
   using L = Layout<N_>;
   using SM = SpectrumSmem<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
@@ -172,19 +235,28 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
   float2* xs = reinterpret_cast<float2*>(smem_raw + SM::XS);   // x[4m + r] at [r][m]; later U_r
   float2* B = reinterpret_cast<float2*>(smem_raw + SM::B);
   float2* twf = reinterpret_cast<float2*>(smem_raw + SM::TWF);
-  const int s = blockIdx.x;
   const int tid = threadIdx.x;
   pdl_launch_dependents();
+  // a plain launch has one CTA per station; a batch launch walks the stations grid-stride
+  const int total = prm.batch ? prm.batch->total_stations : prm.ev0.n_st;
+  for (int gs = blockIdx.x; gs < total; gs += gridDim.x) {
+  const EventDesc* ev = &prm.ev0;
+  if (prm.batch) {
+    const EventDesc* evs = batch_events(prm.batch);
+    ev = evs + find_event(prm.batch->n_events, gs, [&](int e) { return static_cast<long long>(evs[e].station_begin); });
+  }
+  const int s = gs - ev->station_begin;
 
-  const float4* v0 = reinterpret_cast<const float4*>(prm.traces + static_cast<size_t>(s) * 2 * N);
+  const float4* v0 = reinterpret_cast<const float4*>(ev->traces + static_cast<size_t>(s) * 2 * N);
   const float4* v1 = v0 + N / 4;
+  const float2* twf_g = ev->twf;
   for (int m = tid; m < M; m += T) {
     const float4 a = __ldg(v0 + m), b = __ldg(v1 + m);
     xs[0 * M + m] = make_float2(a.x, b.x);
     xs[1 * M + m] = make_float2(a.y, b.y);
     xs[2 * M + m] = make_float2(a.z, b.z);
     xs[3 * M + m] = make_float2(a.w, b.w);
-    twf[m] = __ldg(prm.twf + m);
+    twf[m] = __ldg(twf_g + m);
   }
   __syncthreads();
   // pass 1: task (r, m1), Q-point DFT over m2, twiddle W_M^{m1 k2}
@@ -208,16 +280,18 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
     static_for<0, P>([&](auto k1) { xs[r * M + k2 + Q * k1] = y[k1]; });
   }
   __syncthreads();
-  // the previous kernel in the stream may still read the spectra: wait before writing them
-  pdl_wait_prior();
+  // the previous kernel in the stream may still read these spectra: wait before writing them
+  if (prm.wait_prior) pdl_wait_prior();
   if (s == 0)
-    for (int d = tid; d < prm.n_dir; d += T) prm.dir_done[d] = 0u;
+    for (int d = tid; d < ev->n_dir; d += T) ev->dir_done[d] = 0u;
   // combine the four decimated transforms at k and N - k, split the channels
-  float4* out = prm.spec + static_cast<size_t>(s) * M;
+  float4* out = ev->spec + static_cast<size_t>(s) * M;
+  const float2* wn = ev->wn;
+  const int k_lo = ev->k_lo;
   for (int j = tid; j < M; j += T) {
-    const int k = prm.k_lo + j;
+    const int k = k_lo + j;
     const int kk = k % M, km = (M - kk) % M;
-    const float2 w1 = __ldg(prm.wn + k);                  // W_N^k; W_N^{2k}, W_N^{3k} by products
+    const float2 w1 = __ldg(wn + k);                      // W_N^k; W_N^{2k}, W_N^{3k} by products
     const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
     float2 z = xs[kk], zm = xs[km];
     z = cadd(z, cmul(xs[M + kk], w1));
@@ -230,34 +304,11 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(Spectru
     const float2 dif = make_float2(z.x - zm.x, z.y + zm.y);   // Z[k] - conj Z[N-k]
     out[j] = make_float4(0.5f * sum.x, 0.5f * sum.y, 0.5f * dif.y, -0.5f * dif.x);
   }
+  __syncthreads();   // shared buffers free for the next station
+  }
 }
 
 // ---- K3: fused per-pair unfold + per-direction residual ------------------------------------
-
-struct UnfoldParams {
-  const float4* spec;        // [S][M] station spectra in the band window
-  const float2* table;       // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
-  const int2* binf;          // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
-  const float2* t1;          // [4][Q][P] pass-1 output twiddles
-  const double* dirs;        // [D][2]
-  const double* t_start;     // [S]
-  const double* pos;         // [S][3]
-  float* efield;             // [D][S][2][N] or null
-  float* envelope;           // [D][S][N] or null
-  int* peak_idx;             // [D][S]
-  float* peak_amp;           // [D][S]
-  double* peak_time;         // [D][S]
-  unsigned* status;          // [D][S]
-  double* residual;          // [D][S]
-  double* t0;                // [D]
-  double* chi2;              // [D]
-  unsigned* err;             // device error word
-  unsigned* dir_done;        // [D] pairs finished per direction (zero at launch, reset by its last CTA)
-  double zen0, dzen, az0, daz, dt_ns, n_over_c;
-  int n_zen, n_az, n_f;
-  int n_st, n_dir, k_lo;
-  long long total_pairs;
-};
 
 struct DirInfo {
   int slab0, slab1, slab2, slab3;   // node offsets (units of n_f * 4 float2) of the 4 corners
@@ -267,7 +318,7 @@ struct DirInfo {
 };
 
 // Direction -> pattern cell (FP64, no fused multiply-adds) -> FP32 bilinear weights.
-__device__ __forceinline__ DirInfo direction_cell(const UnfoldParams& p, double zen, double az) {
+__device__ __forceinline__ DirInfo direction_cell(const EventDesc& p, double zen, double az) {
   DirInfo di;
   di.st = 0;
   di.pad = 0;
@@ -334,10 +385,10 @@ struct UnfoldSmem {
   using L = Layout<N_>;
   // byte offsets inside dynamic shared memory (all 16-byte aligned)
   static constexpr size_t A = 0;
-  static constexpr size_t PW = A + sizeof(float2) * L::A_F2;
-  static constexpr size_t SPEC = PW + ((sizeof(float) * L::PW_F + 15) / 16) * 16;
+  static constexpr size_t SPEC = A + sizeof(float2) * L::A_F2;
   static constexpr size_t BINF = SPEC + sizeof(float4) * L::M;
-  static constexpr size_t DIR = BINF + sizeof(int2) * L::M;            // 1 DirInfo
+  static constexpr size_t EV = BINF + sizeof(int2) * L::M;                  // current EventDesc
+  static constexpr size_t DIR = EV + ((sizeof(EventDesc) + 15) / 16) * 16;  // 1 DirInfo
   static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // T/32 x (double, float, int) + flags
   static constexpr size_t BAR = RED + 16 * (L::T / 32) + 32;
   static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2
@@ -363,7 +414,7 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 }
 
 template <int T>
-__device__ __forceinline__ void direction_residual(const UnfoldParams& p, int d, double* red) {
+__device__ __forceinline__ void direction_residual(const EventDesc& p, int d, double* red) {
   const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
   const double sz = sin(zen);
   const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
@@ -392,8 +443,29 @@ __device__ __forceinline__ void direction_residual(const UnfoldParams& p, int d,
   }
 }
 
+// Issue the bulk copies of one pair's inputs: the station's band spectrum and, for a new
+// direction, its four corner slabs (thread 0 only).
+__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, bool new_dir, DirInfo* sdir,
+                                                  float2* slab, float4* sspec, uint64_t* bar, int m) {
+  const unsigned spec_bytes = static_cast<unsigned>(sizeof(float4)) * m;
+  const unsigned slab_bytes = static_cast<unsigned>(ev.n_f) * 4u * sizeof(float2);
+  const size_t node = static_cast<size_t>(ev.n_f) * 4;
+  if (new_dir) {
+    const DirInfo di = direction_cell(ev, ev.dirs[2 * d], ev.dirs[2 * d + 1]);
+    *sdir = di;
+    mbar_arrive_expect_tx(bar, spec_bytes + 4 * slab_bytes);
+    tma_bulk_g2s(slab + 0 * node, ev.table + di.slab0 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 1 * node, ev.table + di.slab1 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 2 * node, ev.table + di.slab2 * node, slab_bytes, bar);
+    tma_bulk_g2s(slab + 3 * node, ev.table + di.slab3 * node, slab_bytes, bar);
+  } else {
+    mbar_arrive_expect_tx(bar, spec_bytes);
+  }
+  tma_bulk_g2s(sspec, ev.spec + static_cast<size_t>(s) * m, spec_bytes, bar);
+}
+
 template <int N_>
-__global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm) {
+__global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_constant__ PathParams prm) {
   using L = Layout<N_>;
   using SM = UnfoldSmem<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
@@ -402,9 +474,9 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* A = reinterpret_cast<float2*>(smem_raw + SM::A);
   float2* E = A;   // E[pol][j], consumed by pass 1 before A is written
-  float* PWX = reinterpret_cast<float*>(smem_raw + SM::PW);
   float4* sspec = reinterpret_cast<float4*>(smem_raw + SM::SPEC);
   int2* sbinf = reinterpret_cast<int2*>(smem_raw + SM::BINF);
+  EventDesc* sev = reinterpret_cast<EventDesc*>(smem_raw + SM::EV);
   DirInfo* sdir = reinterpret_cast<DirInfo*>(smem_raw + SM::DIR);
   double* redd = reinterpret_cast<double*>(smem_raw + SM::RED);      // T/32 doubles
   float* redv = reinterpret_cast<float*>(redd + T / 32);             // T/32 floats
@@ -412,66 +484,81 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
   int* sflag = redi + T / 32;                                        // 1 int
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + SM::BAR);
   float2* slab = reinterpret_cast<float2*>(smem_raw + SM::SLAB);
-  float2* hn = reinterpret_cast<float2*>(smem_raw + SM::hn(prm.n_f));
 
   const int tid = threadIdx.x;
-  const int n_f = prm.n_f;
-  const int S = prm.n_st;
-  pdl_launch_dependents();   // the next kernel may start its prologue as CTAs retire
-  const unsigned slab_bytes = static_cast<unsigned>(n_f) * 4u * sizeof(float2);
-  constexpr unsigned spec_bytes = sizeof(float4) * M;
-  const size_t node = static_cast<size_t>(n_f) * 4;
 
-  // contiguous chunk of the direction-major pair space (q = d * S + s)
-  const long long per = prm.total_pairs / gridDim.x, rem = prm.total_pairs % gridDim.x;
+  // the launch's events and the contiguous chunk of its flattened pair space for this CTA
+  const EventDesc* evs = prm.batch ? batch_events(prm.batch) : &prm.ev0;
+  const int n_events = prm.batch ? prm.batch->n_events : 1;
+  const long long total_pairs =
+      prm.batch ? prm.batch->total_pairs : static_cast<long long>(prm.ev0.n_st) * prm.ev0.n_dir;
+  const long long per = total_pairs / gridDim.x, rem = total_pairs % gridDim.x;
   const long long q0 = blockIdx.x * per + min(static_cast<long long>(blockIdx.x), rem);
   const long long q1 = q0 + per + (blockIdx.x < rem ? 1 : 0);
+  // The station spectra come from an earlier kernel: wait for the previous kernel when asked
+  // to, and let the next kernel in the stream launch only after that, so that a later kernel
+  // launched behind this one may rely on everything this one waited for.
+  if (prm.wait_prior) pdl_wait_prior();
+  pdl_launch_dependents();
   if (q0 >= q1) return;
+  const int e0 = find_event(n_events, q0, [&](int e) { return evs[e].pair_begin; });
 
-  for (int j = tid; j < M; j += T) sbinf[j] = __ldg(prm.binf + j);
+  // walk state, identical in every thread: event e, direction d, station s of pair q
+  int e = e0, d, s;
+  {
+    const long long lq = q0 - evs[e0].pair_begin;
+    d = static_cast<int>(lq / evs[e0].n_st);
+    s = static_cast<int>(lq % evs[e0].n_st);
+  }
   if (tid == 0) {
     mbar_init(bar, 1);
-    const int d = static_cast<int>(q0 / S), s = static_cast<int>(q0 % S);
-    const DirInfo di = direction_cell(prm, prm.dirs[2 * d], prm.dirs[2 * d + 1]);
-    *sdir = di;
-    mbar_arrive_expect_tx(bar, 4 * slab_bytes + spec_bytes);
-    tma_bulk_g2s(slab + 0 * node, prm.table + di.slab0 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 1 * node, prm.table + di.slab1 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 2 * node, prm.table + di.slab2 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 3 * node, prm.table + di.slab3 * node, slab_bytes, bar);
-    pdl_wait_prior();   // the station spectra come from the previous kernel
-    tma_bulk_g2s(sspec, prm.spec + static_cast<size_t>(s) * M, spec_bytes, bar);
+    issue_pair_copies(evs[e0], d, s, true, sdir, slab, sspec, bar, M);
   }
-  pdl_wait_prior();
-  __syncthreads();   // barrier initialised, first direction and frequency cells visible
+  __syncthreads();    // barrier initialised, first direction visible
 
+  int cur_e = e0 - 1;        // event of the previous pair (none yet)
   int cur_d = -1;
   int pairs_in_dir = 0;
   DirInfo di;
+  float2* hn = nullptr;
   unsigned phase = 0;
   for (long long q = q0; q < q1; ++q, phase ^= 1u) {
-    const int d = static_cast<int>(q / S), s = static_cast<int>(q % S);
     const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(prm.err, kErrTmaTimeout);
+    if (__syncthreads_or(!ok)) {   // a bulk copy never completed: report, give it one more bounded wait, leave
+      if (tid == 0) {
+        atomicOr(prm.err, kErrTmaTimeout);
+        mbar_wait_bounded(bar, phase, kWaitLimitNs);
+      }
+      __syncthreads();
       return;
     }
-    if (d != cur_d) {   // new direction: angular (bilinear) interpolation at every frequency node
+    if (e != cur_e) {   // new event: its descriptor and frequency cells into shared memory
+      copy_event(sev, evs + e, tid, T);
+      __syncthreads();
+      for (int j = tid; j < M; j += T) sbinf[j] = __ldg(sev->binf + j);
+    }
+    const EventDesc& ev = *sev;
+    const int S = ev.n_st;
+    if (e != cur_e || d != cur_d) {   // new direction: angular (bilinear) interpolation per frequency node
       di = *sdir;
-      const auto bilin = [&](int e) {
-        const float2 a = slab[e], b = slab[node + e], c = slab[2 * node + e], dd = slab[3 * node + e];
+      const int n_f = ev.n_f;
+      const size_t node = static_cast<size_t>(n_f) * 4;
+      hn = reinterpret_cast<float2*>(smem_raw + SM::hn(n_f));
+      const auto bilin = [&](int x) {
+        const float2 a = slab[x], b = slab[node + x], c = slab[2 * node + x], dd = slab[3 * node + x];
         float2 h;
         h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
         h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
         return h;
       };
-      for (int e = tid; e < n_f * 4; e += T) {
-        const int f = e >> 2, cp = e & 3;
-        const float2 h = bilin(e);
-        const float2 h1 = f + 1 < n_f ? bilin(e + 4) : h;
+      for (int x = tid; x < n_f * 4; x += T) {
+        const int f = x >> 2, cp = x & 3;
+        const float2 h = bilin(x);
+        const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
         hn[8 * f + cp] = h;
         hn[8 * f + 4 + cp] = csub(h1, h);
       }
+      cur_e = e;
       cur_d = d;
       __syncthreads();
     }
@@ -513,23 +600,21 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       E[M + j] = ep;
     }
     const bool any_sing = __syncthreads_or(sing);   // spectrum and slab buffers free from here
-    if (tid == 0 && q + 1 < q1) {                    // prefetch the next pair's inputs
-      const int dn = static_cast<int>((q + 1) / S), sn = static_cast<int>((q + 1) % S);
-      unsigned bytes = spec_bytes;
-      fence_proxy_async_smem();
-      if (dn != d) {
-        const DirInfo nx = direction_cell(prm, prm.dirs[2 * dn], prm.dirs[2 * dn + 1]);
-        *sdir = nx;
-        bytes += 4 * slab_bytes;
-        mbar_arrive_expect_tx(bar, bytes);
-        tma_bulk_g2s(slab + 0 * node, prm.table + nx.slab0 * node, slab_bytes, bar);
-        tma_bulk_g2s(slab + 1 * node, prm.table + nx.slab1 * node, slab_bytes, bar);
-        tma_bulk_g2s(slab + 2 * node, prm.table + nx.slab2 * node, slab_bytes, bar);
-        tma_bulk_g2s(slab + 3 * node, prm.table + nx.slab3 * node, slab_bytes, bar);
-      } else {
-        mbar_arrive_expect_tx(bar, bytes);
+
+    // the next pair of this CTA: next station, else next direction, else the next event
+    const bool has_next = q + 1 < q1;
+    int e_next = e, d_next = d, s_next = s + 1;
+    if (s_next == S) {
+      s_next = 0;
+      if (++d_next == ev.n_dir) {
+        d_next = 0;
+        ++e_next;
       }
-      tma_bulk_g2s(sspec, prm.spec + static_cast<size_t>(sn) * M, spec_bytes, bar);
+    }
+    const bool dir_end = !has_next || e_next != e || d_next != d;
+    if (tid == 0 && has_next) {   // prefetch the next pair's inputs
+      fence_proxy_async_smem();
+      issue_pair_copies(e_next != e ? evs[e_next] : ev, d_next, s_next, dir_end, sdir, slab, sspec, bar, M);
     }
 
     // ---- pass 1: Q-point DFTs per (pol, r, ja) ----
@@ -539,9 +624,9 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       const int ja = tid % P;
       float2 x[Q];
       const float2* Ep = E + pol * M;
-      pass1_task<N_>(Ep, ja, r, prm.t1, x);
+      pass1_task<N_>(Ep, ja, r, ev.t1, x);
       __syncthreads();   // every E read done: A may overwrite it
-      const int row = (prm.k_lo + ja) % P;
+      const int row = (ev.k_lo + ja) % P;
       float2* dst = A + (pol * 4 + r) * PLN + row * LDA;
       static_for<0, Q>([&](auto mb) { dst[mb] = x[mb]; });
     }
@@ -560,8 +645,8 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
         const float2* src = A + (pol * 4 + r) * PLN + mb;
         static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
         dft<P, +1>(y);
-        if (prm.efield) {
-          float* ef = prm.efield + (pair * 2 + pol) * N + tid;
+        if (ev.efield) {
+          float* ef = ev.efield + (pair * 2 + pol) * N + tid;
           static_for<0, P>([&](auto ma) { st_stream(ef + T * ma, y[ma].x); });
         }
         if (pol == 0) {
@@ -570,7 +655,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
           static_for<0, P>([&](auto ma) { pw[ma] += cabs2(y[ma]); });
         }
       }
-      float* en = prm.envelope ? prm.envelope + pair * N + tid : nullptr;
+      float* en = ev.envelope ? ev.envelope + pair * N + tid : nullptr;
       static_for<0, P>([&](auto ma) {
         const float v = sqrt_approx(pw[ma]);
         if (en) st_stream(en + T * ma, v);
@@ -585,27 +670,33 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
       const float2* src = A + (pol * 4 + r) * PLN + mb;
       static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
       dft<P, +1>(y);
-      if (prm.efield) {
-        float* ef = prm.efield + (pair * 2 + pol) * N + tq;
+      if (ev.efield) {
+        float* ef = ev.efield + (pair * 2 + pol) * N + tq;
         static_for<0, P>([&](auto ma) { st_stream(ef + TQ * ma, y[ma].x); });
       }
       float pw[P];
-      static_for<0, P>([&](auto ma) {
-        pw[ma] = cabs2(y[ma]);
-        PWX[(pol * P + ma) * TQ + tq] = pw[ma];
-      });
+      static_for<0, P>([&](auto ma) { pw[ma] = cabs2(y[ma]); });
+      // exchange through A (every thread has read it): the theta threads publish the powers of
+      // samples ma in [P/2, P), the phi threads those of [0, P/2); each side then forms the
+      // envelope of the half it keeps. Layout [P][TQ] floats, row = ma.
       __syncthreads();
-      float* en = prm.envelope ? prm.envelope + pair * N + tq : nullptr;
-      const float* other = PWX + (1 - pol) * P * TQ + tq;
+      float* xch = reinterpret_cast<float*>(A);
+      if (pol == 0) {
+        static_for<P / 2, P>([&](auto ma) { xch[ma * TQ + tq] = pw[ma]; });
+      } else {
+        static_for<0, P / 2>([&](auto ma) { xch[ma * TQ + tq] = pw[ma]; });
+      }
+      __syncthreads();
+      float* en = ev.envelope ? ev.envelope + pair * N + tq : nullptr;
       if (pol == 0) {
         static_for<0, P / 2>([&](auto ma) {
-          const float v = sqrt_approx(pw[ma] + other[ma * TQ]);
+          const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
           if (en) st_stream(en + TQ * ma, v);
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       } else {
         static_for<P / 2, P>([&](auto ma) {
-          const float v = sqrt_approx(pw[ma] + other[ma * TQ]);
+          const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
           if (en) st_stream(en + TQ * ma, v);
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
@@ -621,20 +712,19 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
     if ((tid & 31) == 0) { redv[tid >> 5] = bv; redi[tid >> 5] = bi; }
     __syncthreads();
     ++pairs_in_dir;
-    const bool dir_end = (q + 1 == q1) || ((q + 1) / S != d);
     if (tid == 0) {
 #pragma unroll
       for (int w = 1; w < T / 32; ++w) {
         if (redv[w] > bv || (redv[w] == bv && redi[w] < bi)) { bv = redv[w]; bi = redi[w]; }
       }
       if (bv < 0.f) { bv = 0.f; bi = 0; }
-      prm.peak_idx[pair] = bi;
-      prm.peak_amp[pair] = bv;
-      prm.peak_time[pair] = __dadd_rn(prm.t_start[s], __dmul_rn(static_cast<double>(bi), prm.dt_ns));
-      prm.status[pair] = di.st | (any_sing ? kStSingular : 0u);
+      ev.peak_idx[pair] = bi;
+      ev.peak_amp[pair] = bv;
+      ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+      ev.status[pair] = di.st | (any_sing ? kStSingular : 0u);
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
         __threadfence();
-        const unsigned before = atomicAdd(prm.dir_done + d, static_cast<unsigned>(pairs_in_dir));
+        const unsigned before = atomicAdd(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
         *sflag = (before + pairs_in_dir == static_cast<unsigned>(S)) ? 1 : 0;
         __threadfence();
       }
@@ -642,9 +732,12 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(UnfoldParams prm)
     if (dir_end) {
       pairs_in_dir = 0;
       __syncthreads();
-      if (*sflag) direction_residual<T>(prm, d, redd);
+      if (*sflag) direction_residual<T>(ev, d, redd);
     }
-    __syncthreads();   // A, reductions free for the next pair
+    __syncthreads();   // A, reductions and the event copy free for the next pair
+    e = e_next;
+    d = d_next;
+    s = s_next;
   }
 }
 

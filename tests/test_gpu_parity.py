@@ -175,3 +175,25 @@ def test_argument_validation(ctx, pid):
     with pytest.raises(binding.ArError) as e:
         binding.ar_unfold(ctx.h, binding.make_event(pid, tr, pos, ts, dirs), st)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n,s,d", [(1024, 124, 16), (4096, 40, 16), (2048, 124, 12)])
+def test_parity_many_pairs_per_cta(ctx, pat, pid, n, s, d):
+    """More pairs than resident CTAs, so every CTA walks several pairs (and directions):
+    sampled pairs against the oracle, every direction's residual from the GPU's peaks."""
+    rng = np.random.default_rng(n + s + d)
+    ev = synth.make_event(s, n, synth.random_directions(d, rng), seed_key=30 + n)
+    gpu = run_gpu(ctx, pid, ev)
+    q = np.concatenate([[0, s * d - 1], rng.choice(s * d, 30, replace=False)])
+    di, si = q // s, q % s
+    ref = oracle.unfold_sample(pat, ev, si, di)
+    sub = {k: gpu[k][di, si] for k in ("efield", "envelope", "peak_idx", "peak_amp", "status")}
+    check_pairs(sub, ref, n)
+    check_times(gpu["peak_time_ns"][di, si], ref["peak_time_ns"], "peak time")
+    env, amp, idx = gpu["envelope"], gpu["peak_amp"], gpu["peak_idx"]
+    assert np.all(env.max(axis=2) == amp)
+    assert np.array_equal(np.argmax(env == amp[..., None], axis=2), idx)
+    for dd in range(d):
+        r, t0, chi2 = oracle.residual(ev.pos_m, gpu["peak_time_ns"][dd], *ev.dirs_rad[dd])
+        check_times(gpu["residual_ns"][dd], r, "residual")
+        assert abs(gpu["chi2"][dd] - chi2) <= 1e-9 * max(chi2, 1.0)
