@@ -212,6 +212,52 @@ ar_status ar_batch_tuning(const ar_batch* plan, int32_t* ctas_per_sm, float* can
 /* Wait for the plan's runs in flight and free it. NULL is a no-op. */
 ar_status ar_batch_destroy(ar_batch* plan);
 
+/* ---- serving: continuous batching ----
+ *
+ * A server accepts events whose arrays (inputs and outputs) are in HOST memory and returns
+ * a ticket. A server thread admits queued events in arrival order while their device state
+ * (inputs and outputs on the device) fits the state budget, copies the inputs in, runs the
+ * admitted events as one batch launch and copies the outputs back, on three streams. With two
+ * launches in flight, events that arrive while the GPU is busy join the next launch as memory
+ * frees up, and its copies overlap the running launch. Results do not depend on which other
+ * events share a launch (identical bit for bit alone and in the mix). */
+typedef struct ar_server ar_server;
+
+typedef struct ar_server_config {
+  uint64_t state_budget_bytes;     /* device memory for admitted events; 0 = the context's budget */
+  int32_t max_batch_events;        /* events per launch; 1 with max_inflight 1 = plain serving    */
+  int32_t max_inflight;            /* launches in flight: 1 or 2                                  */
+  int32_t max_stations_per_event;  /* larger events are refused at submit (AR_ERR_BUDGET)         */
+  int32_t max_n_freq;              /* largest frequency-node count of the patterns used           */
+} ar_server_config;
+
+/* Start a server on ctx (allocates the state budget on the device, a batch plan and a server
+ * thread). Errors: AR_ERR_INVALID_ARG, AR_ERR_OUT_OF_MEMORY, AR_ERR_CUDA. */
+ar_status ar_server_create(ar_ctx* ctx, const ar_server_config* cfg, ar_server** server);
+
+/* Queue one event. ev's arrays and out's arrays are HOST memory that must stay valid and
+ * untouched until the ticket completes (pinned memory makes the copies asynchronous).
+ * Directions per event <= 256. Errors: validation as ar_unfold; AR_ERR_BUDGET when the event
+ * can never fit the state budget or the per-event limits. */
+ar_status ar_submit(ar_server* server, const ar_event* ev, const ar_outputs* out, uint64_t* ticket);
+
+/* AR_OK once the ticket's outputs are in place, AR_ERR_NOT_READY before, or the error that
+ * ended it. Unknown ticket: AR_ERR_INVALID_ARG. */
+ar_status ar_poll(ar_server* server, uint64_t ticket);
+
+/* Block until the ticket completes (returns as ar_poll) or timeout_ms passes
+ * (AR_ERR_TIMEOUT; the request stays queued). */
+ar_status ar_wait(ar_server* server, uint64_t ticket, int32_t timeout_ms);
+
+/* Host steady-clock times (ns) of the ticket's submission and completion (0 if not done). */
+ar_status ar_ticket_times(ar_server* server, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns);
+
+/* Forget a completed ticket (its record is kept until then). */
+ar_status ar_ticket_release(ar_server* server, uint64_t ticket);
+
+/* Finish every queued and running event, stop the thread, free the server. NULL is a no-op. */
+ar_status ar_server_destroy(ar_server* server);
+
 /* ar_unfold without any device allocation, for callers that cannot call cudaMalloc: a
  * real-time acquisition loop whose device memory map is fixed after start-up, or a plug-in
  * running inside another program's CUDA context and memory pool. The paper has no

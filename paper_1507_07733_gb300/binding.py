@@ -30,7 +30,9 @@ AR_STATUS_BAD_DIR = 4
 #: every symbol include/aerafold.h declares
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
-            "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy"]
+            "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy",
+            "ar_server_create", "ar_submit", "ar_poll", "ar_wait", "ar_ticket_times", "ar_ticket_release",
+            "ar_server_destroy"]
 
 
 class LibraryMissing(RuntimeError):
@@ -64,6 +66,12 @@ class ar_event(ctypes.Structure):
 
 class ar_batch_limits(ctypes.Structure):
     _fields_ = [("max_events", ctypes.c_int32), ("max_stations", ctypes.c_int32), ("max_dirs", ctypes.c_int32),
+                ("max_n_freq", ctypes.c_int32)]
+
+
+class ar_server_config(ctypes.Structure):
+    _fields_ = [("state_budget_bytes", ctypes.c_uint64), ("max_batch_events", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("max_stations_per_event", ctypes.c_int32),
                 ("max_n_freq", ctypes.c_int32)]
 
 
@@ -106,6 +114,14 @@ def load(path: str | None = None):
         L.ar_batch_run.argtypes = [vp, vp, vp, i32, vp]
         L.ar_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
         L.ar_batch_destroy.argtypes = [vp]
+        u64, i64 = ctypes.c_uint64, ctypes.c_int64
+        L.ar_server_create.argtypes = [vp, ctypes.POINTER(ar_server_config), ctypes.POINTER(vp)]
+        L.ar_submit.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), ctypes.POINTER(u64)]
+        L.ar_poll.argtypes = [vp, u64]
+        L.ar_wait.argtypes = [vp, u64, i32]
+        L.ar_ticket_times.argtypes = [vp, u64, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.ar_ticket_release.argtypes = [vp, u64]
+        L.ar_server_destroy.argtypes = [vp]
         L.ar_unfold_noalloc.argtypes = [ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(ar_event),
                                         ctypes.POINTER(ar_outputs), vp]
         for name in EXPORTED:
@@ -215,6 +231,43 @@ def ar_batch_tuning(plan):
 
 def ar_batch_destroy(plan) -> None:
     load().ar_batch_destroy(plan)
+
+
+def ar_server_create(ctx, state_budget_bytes: int = 0, max_batch_events: int = 32, max_inflight: int = 2,
+                     max_stations_per_event: int = 124, max_n_freq: int = 64):
+    h = ctypes.c_void_p()
+    cfg = ar_server_config(state_budget_bytes, max_batch_events, max_inflight, max_stations_per_event, max_n_freq)
+    _check(ctx, load().ar_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def ar_submit(ctx, server, ev: ar_event, out: ar_outputs) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, load().ar_submit(server, ctypes.byref(ev), ctypes.byref(out), ctypes.byref(t)))
+    return t.value
+
+
+def ar_poll(server, ticket: int) -> int:
+    """Status code: 0 done, 8 (AR_ERR_NOT_READY) in flight, else the request's error."""
+    return load().ar_poll(server, ticket)
+
+
+def ar_wait(server, ticket: int, timeout_ms: int) -> int:
+    return load().ar_wait(server, ticket, timeout_ms)
+
+
+def ar_ticket_times(server, ticket: int):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    st = load().ar_ticket_times(server, ticket, ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
+
+
+def ar_ticket_release(server, ticket: int) -> int:
+    return load().ar_ticket_release(server, ticket)
+
+
+def ar_server_destroy(server) -> None:
+    load().ar_server_destroy(server)
 
 
 # ---- PyTorch-facing helpers ----------------------------------------------------------
@@ -342,6 +395,43 @@ class Batch:
     def close(self):
         if self.h:
             ar_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A continuous-batching server (ar_server_*) on a Context: events and outputs in host
+    (preferably pinned) tensors."""
+
+    def __init__(self, ctx: Context, state_budget_bytes: int = 0, max_batch_events: int = 32, max_inflight: int = 2,
+                 max_stations_per_event: int = 124, max_n_freq: int = 64):
+        self.ctx = ctx
+        self.h = ar_server_create(ctx.h, state_budget_bytes, max_batch_events, max_inflight, max_stations_per_event,
+                                  max_n_freq)
+
+    def submit(self, ev: ar_event, out) -> int:
+        return ar_submit(self.ctx.h, self.h, ev, out if isinstance(out, ar_outputs) else outputs_struct(out))
+
+    def poll(self, ticket: int) -> int:
+        return ar_poll(self.h, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        return ar_wait(self.h, ticket, timeout_ms)
+
+    def times(self, ticket: int):
+        return ar_ticket_times(self.h, ticket)
+
+    def release(self, ticket: int) -> int:
+        return ar_ticket_release(self.h, ticket)
+
+    def close(self):
+        if self.h:
+            ar_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

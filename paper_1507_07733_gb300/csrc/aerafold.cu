@@ -10,10 +10,15 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/aerafold.h"
@@ -51,6 +56,7 @@ std::string g_create_error;
 }  // namespace
 
 struct ar_ctx {
+  std::recursive_mutex mu;   // guards the message and the table caches (a server thread shares them)
   int device = 0;
   int num_sms = 0;
   ar_config cfg{};
@@ -80,7 +86,10 @@ ar_status fail(ar_ctx* ctx, ar_status st, const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
-  if (ctx) ctx->last_error = buf;
+  if (ctx) {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->last_error = buf;
+  }
   return st;
 }
 
@@ -148,6 +157,7 @@ ar_status build_len_tables(ar_ctx* ctx, int k_lo, LenTables* lt) {
 }
 
 ar_status get_len_tables(ar_ctx* ctx, int n, int k_lo, LenTables** out) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   auto key = std::make_pair(n, k_lo);
   auto it = ctx->len_tables.find(key);
   if (it == ctx->len_tables.end()) {
@@ -164,6 +174,7 @@ ar_status get_len_tables(ar_ctx* ctx, int n, int k_lo, LenTables** out) {
 
 // per window bin: frequency cell of the pattern (or -1 outside the band) and its fraction
 ar_status get_bin_table(ar_ctx* ctx, int n, double fs, int pid, int k_lo, int2** out) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   auto key = std::make_tuple(n, fs, pid);
   auto it = ctx->bin_tables.find(key);
   if (it == ctx->bin_tables.end()) {
@@ -226,6 +237,7 @@ ar_status ensure_spec(ar_ctx* ctx, size_t bytes) {
 
 template <int N_>
 ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
   auto key = std::make_pair(N_, n_f);
   auto it = ctx->unfold_cfg.find(key);
   if (it == ctx->unfold_cfg.end()) {
@@ -922,6 +934,422 @@ ar_status ar_batch_tuning(const ar_batch* b, int32_t* ctas_per_sm, float* candid
   for (int c = 0; c < kClasses; ++c) ctas_per_sm[c] = b->ctas_per_sm[c];
   if (candidate_ms)
     for (int k = 0; k < 4; ++k) candidate_ms[k] = b->tune_ms[k + 1];
+  return AR_OK;
+}
+
+}  // extern "C"
+
+// ---- serving: continuous batching of host-buffer requests -------------------------------
+//
+// ar_submit hands the server an event and its outputs in host memory. A server thread admits
+// queued requests in arrival order while their device state (inputs, outputs) fits the state
+// budget, copies their inputs to the device on one stream, runs them as one batch launch on a
+// second stream and copies the outputs back on a third. With two launches in flight, requests
+// that arrive while the GPU is busy are admitted into the next launch as memory frees up; its
+// copies overlap the running launch. Each request's arithmetic does not depend on the batch it
+// ran in, so its results are the same alone and in the mix, bit for bit.
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// first-fit allocator over one device buffer (256-byte granules), coalescing on free
+struct Arena {
+  unsigned char* base = nullptr;
+  size_t size = 0;
+  std::map<size_t, size_t> free_list;   // offset -> length
+  size_t used = 0;
+  void init(unsigned char* b, size_t n) {
+    base = b;
+    size = n;
+    free_list.clear();
+    free_list[0] = n;
+    used = 0;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = (n + 255) / 256 * 256;
+    for (auto it = free_list.begin(); it != free_list.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n;
+        const size_t at = it->first + n;
+        free_list.erase(it);
+        if (rest) free_list[at] = rest;
+        used += n;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = (n + 255) / 256 * 256;
+    used -= n;
+    auto it = free_list.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_list.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_list.erase(nx);
+    }
+    if (it != free_list.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_list.erase(it);
+      }
+    }
+  }
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  ar_event ev{};        // host arrays
+  ar_outputs out{};     // host arrays
+  size_t state_bytes = 0;
+  size_t off = 0;       // arena offset of its device state
+  ar_event dev_ev{};
+  ar_outputs dev_out{};
+  int64_t t_submit = 0, t_done = 0;
+  ar_status status = AR_ERR_NOT_READY;
+};
+
+struct Launch {
+  std::vector<uint64_t> tickets;
+  cudaEvent_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+  bool busy = false;
+};
+
+size_t req_state_bytes(const ar_event& ev, const ar_outputs& out) {
+  const size_t S = ev.n_stations, D = ev.n_dirs, N = ev.n_samples;
+  auto r = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t b = r(S * 2 * N * 4) + r(S * 24) + r(S * 8) + r(D * 16);
+  if (out.efield) b += r(D * S * 2 * N * 4);
+  if (out.envelope) b += r(D * S * N * 4);
+  b += r(D * S * 4) * 2 + r(D * S * 8) * 2 + r(D * 8) * 2 + r(D * S * 4);
+  return b;
+}
+
+}  // namespace
+
+struct ar_server {
+  ar_ctx* ctx = nullptr;
+  ar_server_config cfg{};
+  ar_batch* plan = nullptr;
+  unsigned char* dev_state = nullptr;
+  Arena arena;
+  cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+  std::vector<Launch> launches;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;                          // submitted, not admitted
+  std::unordered_map<uint64_t, Request> reqs;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  std::string error;
+};
+
+namespace {
+
+// device layout of one request's state inside the arena
+void place_request(ar_server* sv, Request& r) {
+  unsigned char* p = sv->arena.base + r.off;
+  const size_t S = r.ev.n_stations, D = r.ev.n_dirs, N = r.ev.n_samples;
+  auto take = [&](size_t n) {
+    unsigned char* q = p;
+    p += (n + 255) / 256 * 256;
+    return q;
+  };
+  r.dev_ev = r.ev;
+  r.dev_ev.traces = reinterpret_cast<const float*>(take(S * 2 * N * 4));
+  r.dev_ev.pos_m = reinterpret_cast<const double*>(take(S * 24));
+  r.dev_ev.t_start_ns = reinterpret_cast<const double*>(take(S * 8));
+  r.dev_ev.dirs_rad = reinterpret_cast<const double*>(take(D * 16));
+  r.dev_out = ar_outputs{};
+  if (r.out.efield) r.dev_out.efield = reinterpret_cast<float*>(take(D * S * 2 * N * 4));
+  if (r.out.envelope) r.dev_out.envelope = reinterpret_cast<float*>(take(D * S * N * 4));
+  r.dev_out.peak_idx = reinterpret_cast<int32_t*>(take(D * S * 4));
+  r.dev_out.peak_amp = reinterpret_cast<float*>(take(D * S * 4));
+  r.dev_out.peak_time_ns = reinterpret_cast<double*>(take(D * S * 8));
+  r.dev_out.residual_ns = reinterpret_cast<double*>(take(D * S * 8));
+  r.dev_out.t0_ns = reinterpret_cast<double*>(take(D * 8));
+  r.dev_out.chi2 = reinterpret_cast<double*>(take(D * 8));
+  r.dev_out.status = reinterpret_cast<uint32_t*>(take(D * S * 4));
+}
+
+cudaError_t copy_in(ar_server* sv, const Request& r) {
+  const size_t S = r.ev.n_stations, D = r.ev.n_dirs, N = r.ev.n_samples;
+  cudaError_t e = cudaMemcpyAsync(const_cast<float*>(r.dev_ev.traces), r.ev.traces, S * 2 * N * 4,
+                                  cudaMemcpyHostToDevice, sv->s_h2d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<double*>(r.dev_ev.pos_m), r.ev.pos_m, S * 24, cudaMemcpyHostToDevice, sv->s_h2d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<double*>(r.dev_ev.t_start_ns), r.ev.t_start_ns, S * 8, cudaMemcpyHostToDevice,
+                        sv->s_h2d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<double*>(r.dev_ev.dirs_rad), r.ev.dirs_rad, D * 16, cudaMemcpyHostToDevice,
+                        sv->s_h2d);
+  return e;
+}
+
+cudaError_t copy_out(ar_server* sv, const Request& r) {
+  const size_t S = r.ev.n_stations, D = r.ev.n_dirs, N = r.ev.n_samples;
+  struct Item { void* h; const void* d; size_t n; };
+  const Item items[] = {{r.out.efield, r.dev_out.efield, D * S * 2 * N * 4},
+                        {r.out.envelope, r.dev_out.envelope, D * S * N * 4},
+                        {r.out.peak_idx, r.dev_out.peak_idx, D * S * 4},
+                        {r.out.peak_amp, r.dev_out.peak_amp, D * S * 4},
+                        {r.out.peak_time_ns, r.dev_out.peak_time_ns, D * S * 8},
+                        {r.out.residual_ns, r.dev_out.residual_ns, D * S * 8},
+                        {r.out.t0_ns, r.dev_out.t0_ns, D * 8},
+                        {r.out.chi2, r.dev_out.chi2, D * 8},
+                        {r.out.status, r.dev_out.status, D * S * 4}};
+  for (const Item& it : items) {
+    if (!it.h || !it.d) continue;
+    cudaError_t e = cudaMemcpyAsync(it.h, it.d, it.n, cudaMemcpyDeviceToHost, sv->s_d2h);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// complete finished launches (lock held)
+void harvest(ar_server* sv) {
+  for (Launch& L : sv->launches) {
+    if (!L.busy || cudaEventQuery(L.d2h) != cudaSuccess) continue;
+    const int64_t t = now_ns();
+    for (uint64_t tk : L.tickets) {
+      Request& r = sv->reqs[tk];
+      sv->arena.release(r.off, r.state_bytes);
+      r.t_done = t;
+      r.status = AR_OK;
+    }
+    L.tickets.clear();
+    L.busy = false;
+    sv->cv_done.notify_all();
+  }
+}
+
+void fail_request(ar_server* sv, Request& r, ar_status st) {
+  r.status = st;
+  r.t_done = now_ns();
+  sv->cv_done.notify_all();
+}
+
+void server_loop(ar_server* sv) {
+  cudaSetDevice(sv->ctx->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    harvest(sv);
+    Launch* slot = nullptr;
+    for (Launch& L : sv->launches)
+      if (!L.busy) { slot = &L; break; }
+    std::vector<uint64_t> batch;
+    if (slot) {
+      // admit in arrival order while the state fits the budget
+      size_t stations = 0, dirs = 0;
+      while (!sv->queue.empty() && static_cast<int>(batch.size()) < sv->cfg.max_batch_events) {
+        Request& r = sv->reqs[sv->queue.front()];
+        if (r.state_bytes > sv->arena.size) {   // can never fit: refuse
+          sv->queue.pop_front();
+          fail_request(sv, r, AR_ERR_BUDGET);
+          continue;
+        }
+        if (stations + r.ev.n_stations > static_cast<size_t>(sv->cfg.max_batch_events) * sv->cfg.max_stations_per_event ||
+            dirs + r.ev.n_dirs > static_cast<size_t>(sv->cfg.max_batch_events) * 256)
+          break;
+        size_t off = 0;
+        if (!sv->arena.alloc(r.state_bytes, &off)) break;   // wait for memory
+        r.off = off;
+        place_request(sv, r);
+        stations += r.ev.n_stations;
+        dirs += r.ev.n_dirs;
+        batch.push_back(r.ticket);
+        sv->queue.pop_front();
+      }
+    }
+    if (batch.empty()) {
+      if (sv->stop && sv->queue.empty()) {
+        bool idle = true;
+        for (Launch& L : sv->launches) idle = idle && !L.busy;
+        if (idle) break;
+      }
+      sv->cv_work.wait_for(lk, std::chrono::microseconds(50));
+      continue;
+    }
+    // launch: inputs in, one batch run, outputs out
+    std::vector<ar_event> evs;
+    std::vector<ar_outputs> outs;
+    cudaError_t e = cudaSuccess;
+    for (uint64_t tk : batch) {
+      const Request& r = sv->reqs[tk];
+      if (e == cudaSuccess) e = copy_in(sv, r);
+      evs.push_back(r.dev_ev);
+      outs.push_back(r.dev_out);
+    }
+    ar_status st = AR_OK;
+    if (e == cudaSuccess) e = cudaEventRecord(slot->h2d, sv->s_h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->s_comp, slot->h2d, 0);
+    if (e == cudaSuccess) st = ar_batch_run(sv->plan, evs.data(), outs.data(), static_cast<int32_t>(evs.size()), sv->s_comp);
+    if (e == cudaSuccess && st == AR_OK) e = cudaEventRecord(slot->comp, sv->s_comp);
+    if (e == cudaSuccess && st == AR_OK) e = cudaStreamWaitEvent(sv->s_d2h, slot->comp, 0);
+    for (uint64_t tk : batch)
+      if (e == cudaSuccess && st == AR_OK) e = copy_out(sv, sv->reqs[tk]);
+    if (e == cudaSuccess && st == AR_OK) e = cudaEventRecord(slot->d2h, sv->s_d2h);
+    if (e != cudaSuccess || st != AR_OK) {
+      sv->error = e != cudaSuccess ? cudaGetErrorString(e) : sv->ctx->last_error;
+      cudaStreamSynchronize(sv->s_h2d);
+      cudaStreamSynchronize(sv->s_comp);
+      cudaStreamSynchronize(sv->s_d2h);
+      for (uint64_t tk : batch) {
+        Request& r = sv->reqs[tk];
+        sv->arena.release(r.off, r.state_bytes);
+        fail_request(sv, r, e != cudaSuccess ? AR_ERR_CUDA : st);
+      }
+      continue;
+    }
+    slot->tickets = batch;
+    slot->busy = true;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ar_status ar_server_create(ar_ctx* ctx, const ar_server_config* cfg, ar_server** out) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (!cfg || !out) return fail(ctx, AR_ERR_INVALID_ARG, "config and output must not be NULL");
+  ar_server_config c = *cfg;
+  if (c.state_budget_bytes == 0) c.state_budget_bytes = ctx->cfg.state_budget_bytes;
+  if (c.max_batch_events < 1 || c.max_batch_events > 4096 || c.max_inflight < 1 || c.max_inflight > 2 ||
+      c.max_stations_per_event < 1 || c.max_n_freq < 2 || c.max_n_freq > kMaxFreqNodes)
+    return fail(ctx, AR_ERR_INVALID_ARG, "server config out of range");
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  ar_server* sv = new ar_server;
+  sv->ctx = ctx;
+  sv->cfg = c;
+  auto cleanup = [&](ar_status st) {
+    ar_server_destroy(sv);
+    return st;
+  };
+  ar_batch_limits lim{c.max_batch_events, c.max_batch_events * c.max_stations_per_event, c.max_batch_events * 256,
+                      c.max_n_freq};
+  ar_status st = ar_batch_create(ctx, &lim, &sv->plan);
+  if (st != AR_OK) return cleanup(st);
+  cudaError_t e = cudaMalloc(&sv->dev_state, c.state_budget_bytes);
+  if (e != cudaSuccess) return cleanup(fail(ctx, AR_ERR_OUT_OF_MEMORY, "state budget allocation failed: %s", cudaGetErrorString(e)));
+  sv->arena.init(sv->dev_state, c.state_budget_bytes);
+  if ((e = cudaStreamCreateWithFlags(&sv->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&sv->s_comp, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&sv->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cleanup(fail(ctx, AR_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e)));
+  sv->launches.resize(c.max_inflight);
+  for (Launch& L : sv->launches) {
+    if ((e = cudaEventCreateWithFlags(&L.h2d, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&L.comp, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&L.d2h, cudaEventDisableTiming)) != cudaSuccess)
+      return cleanup(fail(ctx, AR_ERR_CUDA, "event creation failed: %s", cudaGetErrorString(e)));
+  }
+  sv->worker = std::thread(server_loop, sv);
+  *out = sv;
+  return AR_OK;
+}
+
+ar_status ar_submit(ar_server* sv, const ar_event* ev, const ar_outputs* out, uint64_t* ticket) {
+  if (!sv) return AR_ERR_INVALID_ARG;
+  ar_ctx* ctx = sv->ctx;
+  if (!ticket) return fail(ctx, AR_ERR_INVALID_ARG, "ticket must not be NULL");
+  ar_status st = check_event(ctx, ev, out);
+  if (st != AR_OK) return st;
+  int k_lo = 0;
+  if ((st = validate_shape(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, &k_lo)) != AR_OK) return st;
+  if (ev->n_stations > sv->cfg.max_stations_per_event || ev->n_dirs > 256)
+    return fail(ctx, AR_ERR_BUDGET, "event larger than the server's per-event limits (%d stations, 256 directions)",
+                sv->cfg.max_stations_per_event);
+  Request r;
+  r.ev = *ev;
+  r.out = *out;
+  r.state_bytes = req_state_bytes(*ev, *out);
+  if (r.state_bytes > sv->arena.size)
+    return fail(ctx, AR_ERR_BUDGET, "event state %zu B exceeds the state budget %zu B", r.state_bytes, sv->arena.size);
+  r.t_submit = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return fail(ctx, AR_ERR_INVALID_ARG, "server is shutting down");
+    r.ticket = sv->next_ticket++;
+    *ticket = r.ticket;
+    sv->reqs.emplace(r.ticket, r);
+    sv->queue.push_back(r.ticket);
+  }
+  sv->cv_work.notify_one();
+  return AR_OK;
+}
+
+ar_status ar_poll(ar_server* sv, uint64_t ticket) {
+  if (!sv) return AR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return fail(sv->ctx, AR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  return it->second.status;
+}
+
+ar_status ar_wait(ar_server* sv, uint64_t ticket, int32_t timeout_ms) {
+  if (!sv) return AR_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return fail(sv->ctx, AR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  while (it->second.status == AR_ERR_NOT_READY) {
+    if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second.status == AR_ERR_NOT_READY)
+      return AR_ERR_TIMEOUT;
+  }
+  return it->second.status;
+}
+
+ar_status ar_ticket_times(ar_server* sv, uint64_t ticket, int64_t* submit_ns, int64_t* done_ns) {
+  if (!sv || !submit_ns || !done_ns) return AR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return fail(sv->ctx, AR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  *submit_ns = it->second.t_submit;
+  *done_ns = it->second.t_done;
+  return it->second.status;
+}
+
+ar_status ar_ticket_release(ar_server* sv, uint64_t ticket) {
+  if (!sv) return AR_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return fail(sv->ctx, AR_ERR_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+  if (it->second.status == AR_ERR_NOT_READY) return fail(sv->ctx, AR_ERR_NOT_READY, "ticket still in flight");
+  sv->reqs.erase(it);
+  return AR_OK;
+}
+
+ar_status ar_server_destroy(ar_server* sv) {
+  if (!sv) return AR_OK;
+  if (sv->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    sv->worker.join();
+  }
+  cudaSetDevice(sv->ctx->device);
+  for (Launch& L : sv->launches) {
+    if (L.h2d) cudaEventDestroy(L.h2d);
+    if (L.comp) cudaEventDestroy(L.comp);
+    if (L.d2h) cudaEventDestroy(L.d2h);
+  }
+  if (sv->s_h2d) cudaStreamDestroy(sv->s_h2d);
+  if (sv->s_comp) cudaStreamDestroy(sv->s_comp);
+  if (sv->s_d2h) cudaStreamDestroy(sv->s_d2h);
+  ar_batch_destroy(sv->plan);
+  cudaFree(sv->dev_state);
+  delete sv;
   return AR_OK;
 }
 
