@@ -97,7 +97,8 @@ typedef struct ar_event {
 } ar_event;
 
 /* Outputs, owned by the caller (DEVICE memory for ar_unfold, HOST memory for
- * ar_unfold_host). efield and envelope may be NULL ("peaks only"); the others are required. */
+ * ar_unfold_host). efield and envelope are both given (16-byte aligned) or both NULL
+ * ("peaks only"); the others are required. */
 typedef struct ar_outputs {
   float* efield;               /* [D][S][2][N]  e_theta, e_phi                             */
   float* envelope;             /* [D][S][N]                                                */

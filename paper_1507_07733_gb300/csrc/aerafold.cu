@@ -418,6 +418,10 @@ ar_status check_event(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out) {
     return fail(ctx, AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
   if (!(ev->refractive_index >= 0.0) || !std::isfinite(ev->refractive_index))
     return fail(ctx, AR_ERR_INVALID_ARG, "refractive_index must be finite and >= 0");
+  if (reinterpret_cast<uintptr_t>(out->efield) % 16 != 0 || reinterpret_cast<uintptr_t>(out->envelope) % 16 != 0)
+    return fail(ctx, AR_ERR_INVALID_ARG, "efield and envelope must be 16-byte aligned");
+  if (!out->efield && out->envelope)
+    return fail(ctx, AR_ERR_INVALID_ARG, "envelope without efield is not supported (give both or neither)");
   return AR_OK;
 }
 
@@ -1534,6 +1538,9 @@ ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const
   if (!out->peak_idx || !out->peak_amp || !out->peak_time_ns || !out->residual_ns || !out->t0_ns || !out->chi2 ||
       !out->status)
     return noalloc_fail(AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
+  if (reinterpret_cast<uintptr_t>(out->efield) % 16 != 0 || reinterpret_cast<uintptr_t>(out->envelope) % 16 != 0 ||
+      (!out->efield && out->envelope))
+    return noalloc_fail(AR_ERR_INVALID_ARG, "efield and envelope must be 16-byte aligned, and given together");
   if (!(ev->fs_hz > 0.0)) return noalloc_fail(AR_ERR_INVALID_ARG, "fs_hz must be positive");
   int lo, cnt, hi;
   band_window(ev->n_samples, ev->fs_hz, &lo, &cnt, &hi);

@@ -61,6 +61,8 @@ struct Layout : Shape<N_> {
   // with SPLIT == 2, the |Y|^2 exchange between the two polarisations' threads, P x 4Q
   // floats, also reuses A once pass 2 has read it
   static_assert(2 * A_F2 >= S::P * 4 * S::Q, "the exchange must fit in A");
+  // outputs staged behind E: 16M bytes of E (or the exchange), then 3N floats
+  static_assert(sizeof(float2) * A_F2 >= 16 * S::M + 12 * S::N, "the output staging must fit in A");
   static_assert(T % 32 == 0 && S::M % T == 0, "layout");
 };
 
@@ -122,16 +124,19 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// read-only load that asks L1 to keep the line (twiddle tables reused by every pair)
-__device__ __forceinline__ float2 ldg_keep(const float2* p) {
-  float2 v;
-  asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-  return v;
+// 1-D bulk copy shared -> global (16-byte aligned, size % 16 == 0), tracked as a bulk group
+__device__ __forceinline__ void tma_bulk_s2g(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
 }
-// streaming store: the output is written once and not read back by the kernel
-__device__ __forceinline__ void st_stream(float* p, float v) {
-  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+__device__ __forceinline__ void tma_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until the committed bulk stores have finished reading shared memory
+__device__ __forceinline__ void tma_bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+// wait until the committed bulk stores are complete
+__device__ __forceinline__ void tma_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // programmatic dependent launch: let the next kernel in the stream start its prologue, and
 // wait for the previous kernel's completion (both are no-ops without the launch attribute)
@@ -359,13 +364,17 @@ __constant__ float2 c_pre32[4][32];
 __constant__ float2 c_pre16[4][16];
 
 // Pass 1 for one (pol, r, ja): load E_p[ja + P jb], pre-twiddle, Q-point inverse DFT, output
-// twiddle T1[r][mb][ja].
+// twiddle T1[r][mb][ja] = w0 v^mb with w0 = T1[r][0][ja], v = T1[0][1][ja] = exp(2 pi i (k_lo+ja) 4/N).
+// The twiddles are formed in registers as w0 (v^4)^i v^j (mb = 4i + j): two table loads per
+// task instead of Q, at most ten roundings deep (relative error ~1e-6, inside the path's 1e-5).
 template <int N_>
 __device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, const float2* __restrict__ t1,
                                            float2 (&x)[Layout<N_>::Q]) {
   using L = Layout<N_>;
   constexpr int Q = L::Q, P = L::P;
   static_assert(Q == 32 || Q == 16, "pre-twiddle tables exist for Q = 16 and 32");
+  const float2 w0 = __ldg(t1 + (r * Q) * P + ja);   // issued early: used after the DFT
+  const float2 v1 = __ldg(t1 + P + ja);
   static_for<0, Q>([&](auto jb) {
     constexpr int JB = decltype(jb)::value;
     const float2 e = Ep[ja + P * JB];
@@ -376,8 +385,16 @@ __device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, cons
     }
   });
   dft<Q, +1>(x);
-  const float2* tw = t1 + (r * Q) * P + ja;
-  static_for<0, Q>([&](auto mb) { x[mb] = cmul(x[mb], ldg_keep(tw + mb * P)); });
+  const float2 v2 = cmul(v1, v1), v3 = cmul(v2, v1), v4 = cmul(v2, v2);
+  float2 a = w0;
+  static_for<0, Q / 4>([&](auto i) {
+    constexpr int I = decltype(i)::value;
+    x[4 * I] = cmul(x[4 * I], a);
+    x[4 * I + 1] = cmul(x[4 * I + 1], cmul(a, v1));
+    x[4 * I + 2] = cmul(x[4 * I + 2], cmul(a, v2));
+    x[4 * I + 3] = cmul(x[4 * I + 3], cmul(a, v3));
+    if constexpr (I + 1 < Q / 4) a = cmul(a, v4);
+  });
 }
 
 template <int N_>
@@ -528,6 +545,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       if (tid == 0) {
         atomicOr(prm.err, kErrTmaTimeout);
         mbar_wait_bounded(bar, phase, kWaitLimitNs);
+        tma_bulk_wait_all();
       }
       __syncthreads();
       return;
@@ -625,6 +643,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       float2 x[Q];
       const float2* Ep = E + pol * M;
       pass1_task<N_>(Ep, ja, r, ev.t1, x);
+      if (tid == 0) tma_bulk_wait_read();   // the previous pair's staged outputs have left A
       __syncthreads();   // every E read done: A may overwrite it
       const int row = (ev.k_lo + ja) % P;
       float2* dst = A + (pol * 4 + r) * PLN + row * LDA;
@@ -633,33 +652,35 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     __syncthreads();
 
     // ---- pass 2: P-point DFTs, E-field, envelope, peak ----
+    // Outputs are staged in shared memory behind E (bytes [16M, 64M) of A: e_theta, e_phi,
+    // envelope, N floats each) and written by two bulk copies; with SPLIT == 2 the |Y|^2
+    // exchange uses the first 16M bytes (where E was).
     const size_t pair = static_cast<size_t>(d) * S + s;
+    const bool traces = ev.efield != nullptr;
+    float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(A) + 16 * M);
     float bv = -1.0f;
     int bi = 0;
     if constexpr (SPLIT == 1) {
       const int r = tid & 3, mb = tid >> 2;
-      float pw[P];
-#pragma unroll 1
-      for (int pol = 0; pol < 2; ++pol) {
-        float2 y[P];
-        const float2* src = A + (pol * 4 + r) * PLN + mb;
-        static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
-        dft<P, +1>(y);
-        if (ev.efield) {
-          float* ef = ev.efield + (pair * 2 + pol) * N + tid;
-          static_for<0, P>([&](auto ma) { st_stream(ef + T * ma, y[ma].x); });
-        }
-        if (pol == 0) {
-          static_for<0, P>([&](auto ma) { pw[ma] = cabs2(y[ma]); });
-        } else {
-          static_for<0, P>([&](auto ma) { pw[ma] += cabs2(y[ma]); });
-        }
-      }
-      float* en = ev.envelope ? ev.envelope + pair * N + tid : nullptr;
+      float2 y0[P], y1[P];
+      const float2* src0 = A + r * PLN + mb;
+      const float2* src1 = A + (4 + r) * PLN + mb;
+      static_for<0, P>([&](auto i) {
+        y0[i] = src0[i * LDA];
+        y1[i] = src1[i * LDA];
+      });
+      __syncthreads();   // every A read done: the staging area may overwrite it
+      dft<P, +1>(y0);
+      dft<P, +1>(y1);
       static_for<0, P>([&](auto ma) {
-        const float v = sqrt_approx(pw[ma]);
-        if (en) st_stream(en + T * ma, v);
-        if (v > bv) { bv = v; bi = tid + T * ma; }
+        const int n = tid + T * ma;
+        const float v = sqrt_approx(fmaf(y0[ma].x, y0[ma].x, y0[ma].y * y0[ma].y) + cabs2(y1[ma]));
+        if (traces) {
+          stage[n] = y0[ma].x;
+          stage[N + n] = y1[ma].x;
+          stage[2 * N + n] = v;
+        }
+        if (v > bv) { bv = v; bi = n; }
       });
     } else {
       constexpr int TQ = 4 * Q;
@@ -669,17 +690,15 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       float2 y[P];
       const float2* src = A + (pol * 4 + r) * PLN + mb;
       static_for<0, P>([&](auto i) { y[i] = src[i * LDA]; });
+      __syncthreads();   // every A read done: the exchange and the staging area may overwrite it
       dft<P, +1>(y);
-      if (ev.efield) {
-        float* ef = ev.efield + (pair * 2 + pol) * N + tq;
-        static_for<0, P>([&](auto ma) { st_stream(ef + TQ * ma, y[ma].x); });
-      }
       float pw[P];
-      static_for<0, P>([&](auto ma) { pw[ma] = cabs2(y[ma]); });
-      // exchange through A (every thread has read it): the theta threads publish the powers of
-      // samples ma in [P/2, P), the phi threads those of [0, P/2); each side then forms the
-      // envelope of the half it keeps. Layout [P][TQ] floats, row = ma.
-      __syncthreads();
+      static_for<0, P>([&](auto ma) {
+        pw[ma] = cabs2(y[ma]);
+        if (traces) stage[pol * N + tq + TQ * ma] = y[ma].x;
+      });
+      // the theta threads publish the powers of samples ma in [P/2, P), the phi threads those
+      // of [0, P/2); each side then forms the envelope of the half it keeps ([P][TQ] floats)
       float* xch = reinterpret_cast<float*>(A);
       if (pol == 0) {
         static_for<P / 2, P>([&](auto ma) { xch[ma * TQ + tq] = pw[ma]; });
@@ -687,17 +706,16 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
         static_for<0, P / 2>([&](auto ma) { xch[ma * TQ + tq] = pw[ma]; });
       }
       __syncthreads();
-      float* en = ev.envelope ? ev.envelope + pair * N + tq : nullptr;
       if (pol == 0) {
         static_for<0, P / 2>([&](auto ma) {
           const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
-          if (en) st_stream(en + TQ * ma, v);
+          if (traces) stage[2 * N + tq + TQ * ma] = v;
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       } else {
         static_for<P / 2, P>([&](auto ma) {
           const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
-          if (en) st_stream(en + TQ * ma, v);
+          if (traces) stage[2 * N + tq + TQ * ma] = v;
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       }
@@ -710,8 +728,14 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
     }
     if ((tid & 31) == 0) { redv[tid >> 5] = bv; redi[tid >> 5] = bi; }
+    if (traces) fence_proxy_async_smem();   // each thread's staged writes, visible to the bulk copy
     __syncthreads();
     ++pairs_in_dir;
+    if (tid == 0 && traces) {   // the staged E-field (both components) and envelope to global memory
+      tma_bulk_s2g(ev.efield + pair * 2 * N, stage, 2 * N * sizeof(float));
+      if (ev.envelope) tma_bulk_s2g(ev.envelope + pair * N, stage + 2 * N, N * sizeof(float));
+      tma_bulk_commit();
+    }
     if (tid == 0) {
 #pragma unroll
       for (int w = 1; w < T / 32; ++w) {
@@ -739,6 +763,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     d = d_next;
     s = s_next;
   }
+  if (tid == 0) tma_bulk_wait_all();
 }
 
 }  // namespace aerafold
