@@ -74,8 +74,10 @@ struct Tw {
 
 // ---- complex helpers ---------------------------------------------------------------------
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract on the (re, im) register pair as one packed FP32x2 instruction
+// (sm_100 and later); a - b is formed as fma(b, -1, a), which rounds like a subtraction.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -135,11 +137,16 @@ template <int SIGN>
 __device__ __forceinline__ void dft4(float2 (&v)[4]) {
   const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
   const float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
-  const float2 jd13 = twmul<1, 4, SIGN>(d13);
   v[0] = cadd(s02, s13);
   v[2] = csub(s02, s13);
-  v[1] = cadd(d02, jd13);
-  v[3] = csub(d02, jd13);
+  // d02 +- SIGN i d13: the rotation mixes components, so these stay scalar
+  if constexpr (SIGN > 0) {
+    v[1] = make_float2(d02.x - d13.y, d02.y + d13.x);
+    v[3] = make_float2(d02.x + d13.y, d02.y - d13.x);
+  } else {
+    v[1] = make_float2(d02.x + d13.y, d02.y - d13.x);
+    v[3] = make_float2(d02.x - d13.y, d02.y + d13.x);
+  }
 }
 
 // R = R1 * R2: input n = n1 + R1 n2, output k = k2 + R2 k1 (decimation in time).
