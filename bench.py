@@ -293,6 +293,11 @@ def run_gpu(args):
         e2e = {"value": round(pairs * world * n_e2e / el, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": round(el / n_e2e * 1e3, 4)}
 
+    single = run_single_event(binding, synth, ctx, pid, dev, stream)
+    precision = None
+    if rank == 0 and not args.no_cpu_baseline:
+        precision = run_precision(binding, synth, ctx, pid, dev)
+
     batched = None
     if not args.no_batch:
         batched = run_batched(args, binding, synth, ctx, pid, dev, stream)
@@ -325,12 +330,88 @@ def run_gpu(args):
             "kernel_ms": {"station_spectrum": round(k1, 5), "unfold_with_residual": round(k3, 5)},
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,
+            "single_event": single,
+            "precision_fp32": precision,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(h0, h1),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_single_event(binding, synth, ctx, pid, dev, stream, reps=200):
+    """The plain single event (10 stations x 2048 samples, one direction): latency-bound.
+    Device time per call (CUDA events around each call), host latency of a synchronous call
+    on device buffers, and of ar_unfold_host (copies both ways)."""
+    import torch
+    ev = synth.single_event(2048)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    e = binding.make_event(pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad), ev.fs_hz)
+    keep = e
+    o, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev)
+    sp = stream.cuda_stream
+    for _ in range(20):
+        binding.ar_unfold(ctx.h, e, ost, sp)
+    torch.cuda.synchronize(dev)
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for i in range(reps):
+        a[i].record(stream)
+        binding.ar_unfold(ctx.h, e, ost, sp)
+        b[i].record(stream)
+    torch.cuda.synchronize(dev)
+    dev_us = sorted(x.elapsed_time(y) * 1e3 for x, y in zip(a, b))
+    host_us = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        binding.ar_unfold(ctx.h, e, ost, sp)
+        binding.ar_sync(ctx.h, sp)
+        host_us.append((time.perf_counter() - t0) * 1e6)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    he = binding.make_event(pid, pin(ev.traces), pin(ev.pos_m), pin(ev.t_start_ns), pin(ev.dirs_rad), ev.fs_hz)
+    ho, host_o = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device="cpu", pin_memory=True)
+    e2e_us = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        binding.ar_unfold_host(ctx.h, he, host_o, sp)
+        e2e_us.append((time.perf_counter() - t0) * 1e6)
+    host_us.sort()
+    e2e_us.sort()
+    med = lambda v: round(v[len(v) // 2], 2)
+    return {"workload": "10 stations x 2 x 2048 samples, 1 direction (zenith 30, azimuth 45)",
+            "device_us_p50": med(dev_us), "device_us_min": round(dev_us[0], 2),
+            "host_sync_us_p50": med(host_us), "host_buffers_us_p50": med(e2e_us),
+            "host_buffers_us_p99": round(e2e_us[int(0.99 * (len(e2e_us) - 1))], 2),
+            "note": "two kernels per call; latency-bound (about 0.25 MB of traffic)"}
+
+
+def run_precision(binding, synth, ctx, pid, dev):
+    """FP32 path against the FP64 oracle on the single event at 4096 samples (and 2048):
+    relative L2 error per pair of the E-field and envelope, peak-index agreement."""
+    import torch
+    import oracle
+    pat = synth.make_pattern()
+    res = {}
+    for n in (4096, 2048):
+        ev = synth.single_event(n)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        out = ctx.unfold(pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad), ev.fs_hz, sync=True)
+        ref = oracle.unfold_event(pat, ev)
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+
+        def rel(a, b, m):
+            a = a.astype(np.float64).reshape(-1, m)
+            b = b.reshape(-1, m)
+            return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+        ef = rel(g["efield"], ref["efield"], 2 * n)
+        en = rel(g["envelope"], ref["envelope"], n)
+        res[str(n)] = {"efield_rel_l2_max": float(ef.max()), "efield_rel_l2_median": float(np.median(ef)),
+                       "envelope_rel_l2_max": float(en.max()),
+                       "peak_idx_equal": int((g["peak_idx"] == ref["peak_idx"]).sum()),
+                       "pairs": int(ef.size),
+                       "residual_abs_max_ns": float(np.abs(g["residual_ns"] - ref["residual_ns"]).max())}
+    return res
 
 
 def run_batched(args, binding, synth, ctx, pid, dev, stream):
