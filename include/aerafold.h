@@ -153,6 +153,31 @@ ar_status ar_prepare(ar_ctx* ctx, int32_t n_samples, double fs_hz, int32_t patte
  * AR_ERR_OUT_OF_MEMORY, AR_ERR_CUDA. */
 ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream);
 
+/* ---- the iterative reconstruction (Sec. 2 of the paper) ----
+ * Initial station times from the voltage maxima (argmax of v0^2 + v1^2); a least-squares
+ * plane-wave fit gives a direction (the paper's triangulation); the E-field of every station
+ * is unfolded for that direction (as ar_unfold with one direction); the envelope maxima give
+ * new times; repeat until the angle between successive fitted directions is below tol_rad,
+ * the station times repeat, or max_iter unfold iterations have run. The fit is unweighted,
+ * linear in (t0, nx, ny) for a fixed nz = sqrt(1 - nx^2 - ny^2), solved in closed form and
+ * repeated four times with nz from the previous solution; FP64 throughout. All pointers are
+ * DEVICE memory; ev->dirs_rad and ev->n_dirs are ignored. The whole loop is queued on stream
+ * with a fixed shape (kernels after convergence return at once), so it can be captured in a
+ * CUDA graph once the shape is prepared. */
+typedef struct ar_recon_out {
+  double* direction;    /* [2] zenith, azimuth of the last fit (NaN if none)                 */
+  double* t0_ns;        /* [1] t0 of the last fit                                           */
+  double* chi2;         /* [1] sum of squared residuals of the last fit, ns^2               */
+  int32_t* iterations;  /* [1] unfold iterations run; -1 if the voltage maxima fit nothing   */
+  double* history;      /* [max_iter + 1][2] direction after each fit, NaN after the last; may be NULL */
+  ar_outputs last;      /* the last unfold's outputs, D = 1 layouts ([1][S] ...)            */
+} ar_recon_out;
+
+/* Errors: as ar_unfold; AR_ERR_INVALID_ARG also for fewer than 3 stations, max_iter outside
+ * [0, 64] or tol_rad < 0. */
+ar_status ar_reconstruct(ar_ctx* ctx, const ar_event* ev, int32_t max_iter, double tol_rad,
+                         const ar_recon_out* out, void* stream);
+
 /* Synchronise stream and report device-side errors raised since the last ar_sync
  * (AR_ERR_DEVICE), then clear them. */
 ar_status ar_sync(ar_ctx* ctx, void* stream);

@@ -63,6 +63,12 @@ def lib():
                                            P, P, I32, P, P, P, P, P, U, P]
             L.orc_unfold_sample.argtypes = [PP, F, I, D, F, P, P, I, I32, I32,
                                             P, P, I32, P, P, U, P]
+            L.orc_voltage_peaks.argtypes = [I, I, D, F, P, I32, P]
+            L.orc_plane_fit.argtypes = [I, P, P, D, P, P, P]
+            L.orc_plane_fit.restype = I
+            L.orc_reconstruct.argtypes = [PP, F, I, I, D, D, F, P, P, I, D, P, I32, P, P, P, P,
+                                          P, P, I32, P, P, U]
+            L.orc_reconstruct.restype = I
             _lib = L
     return _lib
 
@@ -198,3 +204,45 @@ def unfold_sample(pattern, ev, st_idx, dir_idx, traces_out: bool = True) -> dict
                             _p(o["peak_amp"]), _p(o["peak_time_ns"]), _p(o["status"], ctypes.c_uint32),
                             _p(o["min_margin"]))
     return o
+
+
+def voltage_peaks(ev):
+    """Initial timing of the reconstruction loop: per station argmax_n v0^2 + v1^2."""
+    tr = np.ascontiguousarray(ev.traces, dtype=np.float32)
+    idx = np.zeros(ev.n_stations, dtype=np.int32)
+    t = np.empty(ev.n_stations)
+    lib().orc_voltage_peaks(ev.n_stations, ev.n_samples, ev.fs_hz, _p(tr, ctypes.c_float),
+                            _p(np.ascontiguousarray(ev.t_start_ns, dtype=np.float64)), _p(idx, ctypes.c_int32), _p(t))
+    return idx, t
+
+
+def plane_fit(pos, t_ns, n_refr: float = 1.0):
+    """Least-squares plane-wave direction: (zenith, azimuth, t0) or None if undetermined."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    t = np.ascontiguousarray(t_ns, dtype=np.float64)
+    z, a, t0 = np.empty(1), np.empty(1), np.empty(1)
+    if lib().orc_plane_fit(pos.shape[0], _p(pos), _p(t), n_refr, _p(z), _p(a), _p(t0)):
+        return None
+    return float(z[0]), float(a[0]), float(t0[0])
+
+
+def reconstruct(pattern, ev, max_iter: int = 8, tol_rad: float = 1e-6, n_refr: float = 1.0) -> dict:
+    """The iterative loop of Sec. 2 on one event (directions of ``ev`` are ignored)."""
+    pd, table = _pat(pattern)
+    S, N = ev.n_stations, ev.n_samples
+    tr = np.ascontiguousarray(ev.traces, dtype=np.float32)
+    pos = np.ascontiguousarray(ev.pos_m, dtype=np.float64)
+    ts = np.ascontiguousarray(ev.t_start_ns, dtype=np.float64)
+    hist = np.full((max_iter + 1, 2), np.nan)
+    ihist = np.full((max_iter + 1, S), -1, dtype=np.int32)
+    zen, az, t0, chi2 = np.empty(1), np.empty(1), np.empty(1), np.full(1, np.nan)
+    ef, env = np.empty((S, 2, N)), np.empty((S, N))
+    pi, pa, pt = np.zeros(S, dtype=np.int32), np.empty(S), np.empty(S)
+    st = np.zeros(S, dtype=np.uint32)
+    it = lib().orc_reconstruct(ctypes.byref(pd), _p(table, ctypes.c_float), S, N, ev.fs_hz, n_refr,
+                               _p(tr, ctypes.c_float), _p(pos), _p(ts), max_iter, tol_rad, _p(hist),
+                               _p(ihist, ctypes.c_int32), _p(zen), _p(az), _p(t0), _p(chi2), _p(ef), _p(env),
+                               _p(pi, ctypes.c_int32), _p(pa), _p(pt), _p(st, ctypes.c_uint32))
+    return dict(iterations=it, zenith=float(zen[0]), azimuth=float(az[0]), t0_ns=float(t0[0]), chi2=float(chi2[0]),
+                history=hist, peak_idx_history=ihist, efield=ef, envelope=env, peak_idx=pi, peak_amp=pa,
+                peak_time_ns=pt, status=st)

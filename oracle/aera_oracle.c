@@ -309,3 +309,154 @@ void orc_unfold_sample(const orc_pattern *pt, const float *table, int n, double 
     free(spec);
   }
 }
+
+/* ---- iterative reconstruction (Sec. 2) ------------------------------------------------
+ * 1. initial timing: per station the sample where the voltage trace is largest,
+ *    argmax_n v0[n]^2 + v1[n]^2 (lowest index on ties), t_s = t_start + n 1e9/fs;
+ * 2. triangulation: the plane wave t_s = t0 - n.x_s * n_refr / c fitted by least squares;
+ * 3. the antenna pattern evaluated for that direction and every station's E-field unfolded;
+ * 4. the envelope maxima become the new timing; repeat until the direction stops changing.
+ * Readings (the paper gives none of these details): unweighted least squares; the fit is
+ * linear in (t0, nx, ny) for a fixed nz = sqrt(1 - nx^2 - ny^2), solved by Cramer's rule and
+ * repeated ORC_FIT_PASSES times with nz updated from the previous solution (nz = 1 first);
+ * nx^2 + ny^2 > 1 is scaled back to the horizon; convergence when the angle between successive
+ * directions is below tol_rad or the station times repeat. */
+
+#define ORC_FIT_PASSES 4
+
+void orc_voltage_peaks(int n_st, int n, double fs_hz, const float *traces, const double *t_start_ns,
+                       int32_t *idx, double *t_ns) {
+  for (int s = 0; s < n_st; ++s) {
+    const float *v0 = traces + (size_t)s * 2 * n, *v1 = v0 + n;
+    int best = 0;
+    double bv = -1.0;
+    for (int j = 0; j < n; ++j) {
+      double p = (double)v0[j] * v0[j] + (double)v1[j] * v1[j];
+      if (p > bv) { bv = p; best = j; }
+    }
+    idx[s] = best;
+    t_ns[s] = t_start_ns[s] + (double)best * (1e9 / fs_hz);
+  }
+}
+
+/* Least-squares plane-wave direction from station times. Returns 0, or 1 if the stations
+ * do not determine a direction (fewer than 3 or collinear). */
+int orc_plane_fit(int n_st, const double *pos, const double *t_ns, double n_refr, double *zen, double *az,
+                  double *t0) {
+  if (n_st < 3) return 1;
+  double k = n_refr / ORC_C_M_PER_NS;   /* ns per metre */
+  double nx = 0.0, ny = 0.0, nz = 1.0, c0 = 0.0;
+  for (int pass = 0; pass < ORC_FIT_PASSES; ++pass) {
+    /* model y_s = t_s + k nz z_s = c0 - k nx x_s - k ny y_s: unknowns (c0, a, b) with a = -k nx,
+     * b = -k ny; normal equations of the regressors (1, x_s, y_s) */
+    double m[3][3] = {{0}}, r[3] = {0};
+    for (int s = 0; s < n_st; ++s) {
+      double f[3] = {1.0, pos[3 * s], pos[3 * s + 1]};
+      double y = t_ns[s] + k * nz * pos[3 * s + 2];
+      for (int i = 0; i < 3; ++i) {
+        r[i] += f[i] * y;
+        for (int j = 0; j < 3; ++j) m[i][j] += f[i] * f[j];
+      }
+    }
+    double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                 m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                 m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    double scale = m[0][0] * m[1][1] * m[2][2];
+    if (!(fabs(det) > 1e-12 * scale)) return 1;
+    double sol[3];
+    for (int c = 0; c < 3; ++c) {   /* Cramer: replace column c by r */
+      double a[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) a[i][j] = j == c ? r[i] : m[i][j];
+      double dc = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                  a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                  a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+      sol[c] = dc / det;
+    }
+    c0 = sol[0];
+    nx = -sol[1] / k;
+    ny = -sol[2] / k;
+    double h2 = nx * nx + ny * ny;
+    if (h2 > 1.0) {
+      double h = sqrt(h2);
+      nx /= h;
+      ny /= h;
+      h2 = 1.0;
+    }
+    nz = sqrt(1.0 - h2);
+  }
+  *zen = atan2(sqrt(nx * nx + ny * ny), nz);
+  double a = atan2(ny, nx);
+  *az = a < 0.0 ? a + 2.0 * ORC_PI : a;
+  *t0 = c0;
+  return 0;
+}
+
+/* The whole loop for one event. history gets (zenith, azimuth) after every fit (up to
+ * max_iter + 1 entries); peak_idx_hist the station peak indices used by every fit
+ * [(max_iter + 1)][S]. Outputs of the final unfold: efield [S][2][N], env [S][N] (may be
+ * NULL), peak_idx/peak_amp/peak_time/status [S]. Returns the number of unfold iterations, or
+ * -1 if the first fit failed. */
+int orc_reconstruct(const orc_pattern *pt, const float *table, int n_st, int n, double fs_hz, double n_refr,
+                    const float *traces, const double *pos, const double *t_start_ns, int max_iter, double tol_rad,
+                    double *history, int32_t *peak_idx_hist, double *zen_out, double *az_out, double *t0_out,
+                    double *chi2_out, double *efield, double *env, int32_t *peak_idx, double *peak_amp,
+                    double *peak_time, uint32_t *status) {
+  double *spec = (double *)malloc(sizeof(double) * 4 * (size_t)n * n_st);
+  double *t_ns = (double *)malloc(sizeof(double) * n_st);
+  double *res = (double *)malloc(sizeof(double) * n_st);
+  int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * n_st);
+#pragma omp parallel for schedule(dynamic)
+  for (int s = 0; s < n_st; ++s)
+    orc_station_spectrum(n, traces + (size_t)s * 2 * n, spec + (size_t)s * 4 * n);
+  orc_voltage_peaks(n_st, n, fs_hz, traces, t_start_ns, idx, t_ns);
+  double zen = NAN, az = NAN, t0 = NAN;
+  int iters = 0;
+  memcpy(peak_idx_hist, idx, sizeof(int32_t) * n_st);
+  if (orc_plane_fit(n_st, pos, t_ns, n_refr, &zen, &az, &t0)) {
+    iters = -1;
+  } else {
+    history[0] = zen;
+    history[1] = az;
+    double dt_ns = 1e9 / fs_hz;
+    for (int it = 1; it <= max_iter; ++it) {
+#pragma omp parallel for schedule(dynamic)
+      for (int s = 0; s < n_st; ++s) {
+        double amp, mm;
+        orc_unfold_pair(pt, table, n, fs_hz, spec + (size_t)s * 4 * n, zen, az,
+                        efield ? efield + (size_t)s * 2 * n : NULL, env ? env + (size_t)s * n : NULL,
+                        &peak_idx[s], &amp, &status[s], &mm);
+        peak_amp[s] = amp;
+        peak_time[s] = t_start_ns[s] + (double)peak_idx[s] * dt_ns;
+      }
+      iters = it;
+      int same = memcmp(peak_idx, peak_idx_hist + (size_t)(it - 1) * n_st, sizeof(int32_t) * n_st) == 0;
+      memcpy(peak_idx_hist + (size_t)it * n_st, peak_idx, sizeof(int32_t) * n_st);
+      double nzen, naz, nt0;
+      if (orc_plane_fit(n_st, pos, peak_time, n_refr, &nzen, &naz, &nt0)) break;
+      double ax = sin(zen) * cos(az), ay = sin(zen) * sin(az), az_ = cos(zen);
+      double bx = sin(nzen) * cos(naz), by = sin(nzen) * sin(naz), bz = cos(nzen);
+      double dot = ax * bx + ay * by + az_ * bz;
+      double ang = acos(dot > 1.0 ? 1.0 : (dot < -1.0 ? -1.0 : dot));
+      history[2 * it] = nzen;
+      history[2 * it + 1] = naz;
+      int done = same || ang < tol_rad;
+      zen = nzen;
+      az = naz;
+      t0 = nt0;
+      if (done) break;
+    }
+  }
+  if (iters >= 0) {
+    /* chi2 of the final fit with the final station times */
+    double t0r, chi2;
+    const double *tt = iters == 0 ? t_ns : peak_time;
+    orc_residual(n_st, pos, tt, zen, az, n_refr, res, &t0r, &chi2);
+    *chi2_out = chi2;
+  }
+  *zen_out = zen;
+  *az_out = az;
+  *t0_out = t0;
+  free(spec); free(t_ns); free(res); free(idx);
+  return iters;
+}

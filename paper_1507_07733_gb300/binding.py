@@ -32,7 +32,7 @@ EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
             "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy",
             "ar_server_create", "ar_submit", "ar_poll", "ar_wait", "ar_ticket_times", "ar_ticket_release",
-            "ar_server_destroy"]
+            "ar_server_destroy", "ar_reconstruct"]
 
 
 class LibraryMissing(RuntimeError):
@@ -69,17 +69,22 @@ class ar_batch_limits(ctypes.Structure):
                 ("max_n_freq", ctypes.c_int32)]
 
 
-class ar_server_config(ctypes.Structure):
-    _fields_ = [("state_budget_bytes", ctypes.c_uint64), ("max_batch_events", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int32), ("max_stations_per_event", ctypes.c_int32),
-                ("max_n_freq", ctypes.c_int32)]
-
-
 class ar_outputs(ctypes.Structure):
     _fields_ = [("efield", ctypes.c_void_p), ("envelope", ctypes.c_void_p), ("peak_idx", ctypes.c_void_p),
                 ("peak_amp", ctypes.c_void_p), ("peak_time_ns", ctypes.c_void_p),
                 ("residual_ns", ctypes.c_void_p), ("t0_ns", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
                 ("status", ctypes.c_void_p)]
+
+
+class ar_recon_out(ctypes.Structure):
+    _fields_ = [("direction", ctypes.c_void_p), ("t0_ns", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
+                ("iterations", ctypes.c_void_p), ("history", ctypes.c_void_p), ("last", ar_outputs)]
+
+
+class ar_server_config(ctypes.Structure):
+    _fields_ = [("state_budget_bytes", ctypes.c_uint64), ("max_batch_events", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("max_stations_per_event", ctypes.c_int32),
+                ("max_n_freq", ctypes.c_int32)]
 
 
 _lib = None
@@ -122,6 +127,7 @@ def load(path: str | None = None):
         L.ar_ticket_times.argtypes = [vp, u64, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.ar_ticket_release.argtypes = [vp, u64]
         L.ar_server_destroy.argtypes = [vp]
+        L.ar_reconstruct.argtypes = [vp, ctypes.POINTER(ar_event), i32, dbl, ctypes.POINTER(ar_recon_out), vp]
         L.ar_unfold_noalloc.argtypes = [ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(ar_event),
                                         ctypes.POINTER(ar_outputs), vp]
         for name in EXPORTED:
@@ -270,6 +276,11 @@ def ar_server_destroy(server) -> None:
     load().ar_server_destroy(server)
 
 
+def ar_reconstruct(ctx, ev: ar_event, max_iter: int, tol_rad: float, out: ar_recon_out, stream: int = 0) -> None:
+    _check(ctx, load().ar_reconstruct(ctx, ctypes.byref(ev), max_iter, tol_rad, ctypes.byref(out),
+                                      ctypes.c_void_p(stream)))
+
+
 # ---- PyTorch-facing helpers ----------------------------------------------------------
 
 def _ptr(t):
@@ -354,6 +365,30 @@ class Context:
 
     def batch(self, max_events: int, max_stations: int, max_dirs: int, max_n_freq: int = 64) -> "Batch":
         return Batch(self, max_events, max_stations, max_dirs, max_n_freq)
+
+    def reconstruct(self, pattern_id: int, traces, pos_m, t_start_ns, fs_hz: float = 200e6,
+                    refractive_index: float = 1.0, max_iter: int = 8, tol_rad: float = 1e-6, traces_out: bool = True,
+                    stream=None, sync: bool = True) -> dict:
+        """The iterative reconstruction of one event held in device tensors."""
+        import torch
+        S, _, N = traces.shape
+        dev = traces.device
+        last, _ = alloc_outputs(1, S, N, device=dev, traces=traces_out)
+        res = dict(direction=torch.empty(2, dtype=torch.float64, device=dev),
+                   t0_ns=torch.empty(1, dtype=torch.float64, device=dev),
+                   chi2=torch.empty(1, dtype=torch.float64, device=dev),
+                   iterations=torch.empty(1, dtype=torch.int32, device=dev),
+                   history=torch.empty((max_iter + 1, 2), dtype=torch.float64, device=dev))
+        dummy = torch.empty((1, 2), dtype=torch.float64, device=dev)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dummy, fs_hz, refractive_index)
+        out = ar_recon_out(_ptr(res["direction"]), _ptr(res["t0_ns"]), _ptr(res["chi2"]), _ptr(res["iterations"]),
+                           _ptr(res["history"]), outputs_struct(last))
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        ar_reconstruct(self.h, ev, max_iter, tol_rad, out, st.cuda_stream)
+        if sync:
+            ar_sync(self.h, st.cuda_stream)
+        res["last"] = last
+        return res
 
     def sync(self, stream=None) -> None:
         import torch

@@ -69,6 +69,8 @@ struct ar_ctx {
   size_t spec_bytes = 0;
   unsigned* dir_done = nullptr;   // [max directions] completion counters of the fused residual
   size_t dir_cap = 0;
+  unsigned char* recon = nullptr; // reconstruction state, station times and indices
+  size_t recon_bytes = 0;
   unsigned* d_err = nullptr;
   // device staging for ar_unfold_host
   std::vector<std::pair<void*, size_t>> stage;   // slots, grown on demand
@@ -490,6 +492,7 @@ ar_status ar_destroy(ar_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   cudaFree(ctx->spec);
   cudaFree(ctx->dir_done);
+  cudaFree(ctx->recon);
   cudaFree(ctx->d_err);
   delete ctx;
   return AR_OK;
@@ -552,6 +555,99 @@ ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void
     case 2048: return launch_all<2048>(ctx, ev, out, rs, s);
     default: return launch_all<4096>(ctx, ev, out, rs, s);
   }
+}
+
+}  // extern "C"
+
+namespace {
+
+template <int N_>
+cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double tol_rad, const ar_recon_out* out,
+                         const Resolved& rs, ReconState* st, int* vidx, double* vtimes, int* prev_idx,
+                         cudaStream_t stream) {
+  using L = Layout<N_>;
+  const PatternDev& pat = ctx->patterns[ev->pattern_id];
+  ar_event e1 = *ev;
+  e1.n_dirs = 1;
+  e1.dirs_rad = st->dir;   // the direction the last fit produced (device memory)
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  PathParams pp{};
+  pp.batch = nullptr;
+  pp.err = ctx->d_err;
+  pp.skip = &st->converged;
+  pp.wait_prior = 1;
+  pp.ev0 = make_desc(b, pat.desc, pat.table, &e1, &out->last, rs.k_lo);
+  const int S = ev->n_stations;
+  const double dt_ns = 1e9 / ev->fs_hz;
+  const double n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(ReconState), stream);
+  if (e == cudaSuccess && out->history)
+    e = cudaMemsetAsync(out->history, 0xff, sizeof(double) * 2 * (max_iter + 1), stream);   // NaN
+  if (e != cudaSuccess) return e;
+  // the station spectra, once: every iteration unfolds the same traces
+  PathParams sp = pp;
+  sp.skip = nullptr;
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, S, L::T, SpectrumSmem<N_>::TOTAL, stream, sp)) != cudaSuccess)
+    return e;
+  voltage_peak_kernel<<<S, 256, 0, stream>>>(ev->traces, ev->t_start_ns, ev->n_samples, dt_ns, vidx, vtimes);
+  FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
+  plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
+  for (int it = 1; it <= max_iter; ++it) {
+    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T, UnfoldSmem<N_>::total(pat.desc.n_freq),
+                        stream, pp)) != cudaSuccess)
+      return e;
+    fp.times = out->last.peak_time_ns;
+    fp.idx = out->last.peak_idx;
+    fp.iteration = it;
+    plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
+  }
+  recon_finish_kernel<<<1, 32, 0, stream>>>(st, out->direction, out->t0_ns, out->chi2, out->iterations);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+ar_status ar_reconstruct(ar_ctx* ctx, const ar_event* ev, int32_t max_iter, double tol_rad, const ar_recon_out* out,
+                         void* stream) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (!ev || !out) return fail(ctx, AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+  if (max_iter < 0 || max_iter > 64) return fail(ctx, AR_ERR_INVALID_ARG, "max_iter must be in [0, 64]");
+  if (!(tol_rad >= 0.0)) return fail(ctx, AR_ERR_INVALID_ARG, "tol_rad must be >= 0");
+  if (!out->direction || !out->t0_ns || !out->chi2 || !out->iterations)
+    return fail(ctx, AR_ERR_INVALID_ARG, "direction, t0, chi2 and iterations outputs must not be NULL");
+  ar_event e1 = *ev;
+  e1.n_dirs = 1;
+  e1.dirs_rad = reinterpret_cast<const double*>(ev->traces);   // placeholder for validation only
+  ar_status st = check_event(ctx, &e1, &out->last);
+  if (st != AR_OK) return st;
+  if (ev->n_stations < 3) return fail(ctx, AR_ERR_INVALID_ARG, "a direction fit needs at least 3 stations");
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  Resolved rs;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve_dirs(ctx, 1)) != AR_OK) return st;
+  const size_t S = ev->n_stations;
+  const size_t need = 256 + S * (4 + 8 + 4) + 3 * 256;
+  if (need > ctx->recon_bytes) {
+    AR_CUDA(ctx, cudaDeviceSynchronize());
+    cudaFree(ctx->recon);
+    ctx->recon = nullptr;
+    ctx->recon_bytes = 0;
+    AR_CUDA(ctx, cudaMalloc(&ctx->recon, need));
+    ctx->recon_bytes = need;
+  }
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  ReconState* rst = reinterpret_cast<ReconState*>(ctx->recon);
+  double* vtimes = reinterpret_cast<double*>(ctx->recon + 256);
+  int* vidx = reinterpret_cast<int*>(ctx->recon + 256 + up(S * 8));
+  int* prev_idx = reinterpret_cast<int*>(ctx->recon + 256 + up(S * 8) + up(S * 4));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = ev->n_samples == 1024 ? launch_recon<1024>(ctx, ev, max_iter, tol_rad, out, rs, rst, vidx, vtimes, prev_idx, s)
+                  : ev->n_samples == 2048 ? launch_recon<2048>(ctx, ev, max_iter, tol_rad, out, rs, rst, vidx, vtimes, prev_idx, s)
+                                          : launch_recon<4096>(ctx, ev, max_iter, tol_rad, out, rs, rst, vidx, vtimes, prev_idx, s);
+  if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "reconstruction launch failed: %s", cudaGetErrorString(e));
+  return AR_OK;
 }
 
 ar_status ar_sync(ar_ctx* ctx, void* stream) {

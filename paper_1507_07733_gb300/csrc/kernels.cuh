@@ -193,6 +193,7 @@ __host__ __device__ inline const EventDesc* batch_events(const BatchHeader* h) {
 struct PathParams {
   const BatchHeader* batch;   // device batch, or null: the single event ev0
   unsigned* err;              // device error word
+  const int* skip;            // if not null and *skip != 0 the kernel does nothing (a loop has converged)
   int wait_prior;             // wait for the previous kernel in the stream (its results are needed)
   int pad;
   EventDesc ev0;
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
   // launched behind this one may rely on everything this one waited for.
   if (prm.wait_prior) pdl_wait_prior();
   pdl_launch_dependents();
-  if (q0 >= q1) return;
+  if (q0 >= q1 || (prm.skip && *prm.skip)) return;
   const int e0 = find_event(n_events, q0, [&](int e) { return evs[e].pair_begin; });
 
   // walk state, identical in every thread: event e, direction d, station s of pair q
@@ -764,6 +765,204 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     s = s_next;
   }
   if (tid == 0) tma_bulk_wait_all();
+}
+
+// ---- iterative reconstruction (Sec. 2): voltage-maximum timing, plane-wave fit -------------
+
+struct ReconState {        // device memory, one per ar_reconstruct call
+  double dir[2];           // direction the next unfold uses (zenith, azimuth)
+  double t0;
+  double chi2;
+  int converged;           // set when the direction stops changing (or the fit fails)
+  int iterations;          // unfold iterations whose results were fitted
+  int failed;              // the first fit found no direction
+  int pad;
+};
+
+struct FitParams {
+  const double* pos;       // [S][3]
+  const double* times;     // [S] station times to fit (voltage maxima, or the unfold's peak times)
+  const int* idx;          // [S] the sample indices behind those times
+  int* prev_idx;           // [S] the indices of the previous fit (updated here)
+  ReconState* st;
+  double* history;         // [(max_iter + 1)][2] or null
+  double n_over_c, tol_rad;
+  int n_st, iteration;     // iteration 0 fits the voltage maxima
+};
+
+// argmax_n v0[n]^2 + v1[n]^2 per station (FP64 squares, lowest index on ties); one CTA per station
+__global__ void __launch_bounds__(256) voltage_peak_kernel(const float* traces, const double* t_start, int n,
+                                                           double dt_ns, int* idx, double* t_ns) {
+  const int s = blockIdx.x, tid = threadIdx.x;
+  const float* v0 = traces + static_cast<size_t>(s) * 2 * n;
+  const float* v1 = v0 + n;
+  double bv = -1.0;
+  int bi = 0;
+  for (int j = tid; j < n; j += 256) {
+    const double a = v0[j], b = v1[j];
+    const double pw = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+    if (pw > bv) { bv = pw; bi = j; }
+  }
+  __shared__ double rv[8];
+  __shared__ int ri[8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  if ((tid & 31) == 0) { rv[tid >> 5] = bv; ri[tid >> 5] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < 8; ++w)
+      if (rv[w] > bv || (rv[w] == bv && ri[w] < bi)) { bv = rv[w]; bi = ri[w]; }
+    idx[s] = bi;
+    t_ns[s] = __dadd_rn(t_start[s], __dmul_rn(static_cast<double>(bi), dt_ns));
+  }
+}
+
+__device__ __forceinline__ double det3(const double (&a)[3][3]) {
+  return a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+         a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+}
+
+// Least-squares plane wave t_s = t0 - n.x_s n_refr / c: linear in (t0, nx, ny) for a fixed nz,
+// repeated four times with nz from the previous solution (nz = 1 first). One CTA of 128
+// threads, FP64, sums in a fixed order. Also decides convergence and the residual chi2.
+__global__ void __launch_bounds__(128) plane_fit_kernel(FitParams p) {
+  ReconState* st = p.st;
+  if (st->converged) return;
+  const int tid = threadIdx.x;
+  __shared__ double red[4][10];
+  __shared__ double sol[4];
+  __shared__ int same_s;
+  // do the station indices repeat those of the previous fit?
+  int diff = 0;
+  if (p.iteration > 0)
+    for (int s = tid; s < p.n_st; s += 128) diff |= p.idx[s] != p.prev_idx[s];
+  const int any_diff = __syncthreads_or(diff);
+  for (int s = tid; s < p.n_st; s += 128) p.prev_idx[s] = p.idx[s];
+  if (tid == 0) same_s = p.iteration > 0 && !any_diff;
+  const double k = p.n_over_c;
+  double nz = 1.0;
+  bool ok = true;
+  for (int pass = 0; pass < 4 && ok; ++pass) {
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // n, Sx, Sy, Sxx, Sxy, Syy, Sy_t, Sx_t, Sy_t(y)
+    for (int s = tid; s < p.n_st; s += 128) {
+      const double x = p.pos[3 * s], y = p.pos[3 * s + 1], z = p.pos[3 * s + 2];
+      const double yt = __dadd_rn(p.times[s], __dmul_rn(__dmul_rn(k, nz), z));
+      v[0] += 1.0; v[1] += x; v[2] += y; v[3] += x * x; v[4] += x * y; v[5] += y * y;
+      v[6] += yt; v[7] += x * yt; v[8] += y * yt;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double t = v[i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if ((tid & 31) == 0) red[tid >> 5][i] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t[9];
+      for (int i = 0; i < 9; ++i) t[i] = red[0][i] + red[1][i] + red[2][i] + red[3][i];
+      const double m[3][3] = {{t[0], t[1], t[2]}, {t[1], t[3], t[4]}, {t[2], t[4], t[5]}};
+      const double r[3] = {t[6], t[7], t[8]};
+      const double det = det3(m);
+      if (!(fabs(det) > 1e-12 * (m[0][0] * m[1][1] * m[2][2]))) {
+        sol[3] = 0.0;
+      } else {
+        double x[3];
+        for (int c = 0; c < 3; ++c) {
+          double a[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) a[i][j] = j == c ? r[i] : m[i][j];
+          x[c] = det3(a) / det;
+        }
+        double nx = -x[1] / k, ny = -x[2] / k;
+        double h2 = nx * nx + ny * ny;
+        if (h2 > 1.0) {
+          const double h = sqrt(h2);
+          nx /= h;
+          ny /= h;
+          h2 = 1.0;
+        }
+        sol[0] = x[0];
+        sol[1] = nx;
+        sol[2] = ny;
+        sol[3] = 1.0;
+      }
+    }
+    __syncthreads();
+    ok = sol[3] != 0.0;
+    if (ok) nz = sqrt(1.0 - (sol[1] * sol[1] + sol[2] * sol[2]));
+    __syncthreads();
+  }
+  if (!ok) {   // no direction: stop; the first fit failing marks the reconstruction failed
+    if (tid == 0) {
+      st->converged = 1;
+      if (p.iteration == 0) {
+        st->failed = 1;
+        st->dir[0] = st->dir[1] = st->t0 = st->chi2 = __longlong_as_double(0x7ff8000000000000ll);
+      } else {
+        st->iterations = p.iteration;
+      }
+    }
+    return;
+  }
+  const double nx = sol[1], ny = sol[2];
+  const double zen = atan2(sqrt(nx * nx + ny * ny), nz);
+  double az = atan2(ny, nx);
+  if (az < 0.0) az += 2.0 * 3.14159265358979323846;
+  // chi2 of this direction with these times (two-pass mean, as the per-direction residual)
+  const double snx = sin(zen) * cos(az), sny = sin(zen) * sin(az), snz = cos(zen);
+  double acc = 0.0;
+  for (int s = tid; s < p.n_st; s += 128)
+    acc += p.times[s] + (snx * p.pos[3 * s] + sny * p.pos[3 * s + 1] + snz * p.pos[3 * s + 2]) * k;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((tid & 31) == 0) red[tid >> 5][9] = acc;
+  __syncthreads();
+  const double mean = (red[0][9] + red[1][9] + red[2][9] + red[3][9]) / p.n_st;
+  __syncthreads();
+  double ss = 0.0;
+  for (int s = tid; s < p.n_st; s += 128) {
+    const double r = p.times[s] + (snx * p.pos[3 * s] + sny * p.pos[3 * s + 1] + snz * p.pos[3 * s + 2]) * k - mean;
+    ss += r * r;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  if ((tid & 31) == 0) red[tid >> 5][9] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    const double chi2 = red[0][9] + red[1][9] + red[2][9] + red[3][9];
+    bool done = false;
+    if (p.iteration > 0) {
+      const double pz = st->dir[0], pa = st->dir[1];
+      double dot = sin(pz) * cos(pa) * snx + sin(pz) * sin(pa) * sny + cos(pz) * snz;
+      dot = dot > 1.0 ? 1.0 : (dot < -1.0 ? -1.0 : dot);
+      done = same_s || acos(dot) < p.tol_rad;
+      st->iterations = p.iteration;
+    }
+    st->dir[0] = zen;
+    st->dir[1] = az;
+    st->t0 = sol[0];
+    st->chi2 = chi2;
+    if (p.history) {
+      p.history[2 * p.iteration] = zen;
+      p.history[2 * p.iteration + 1] = az;
+    }
+    if (done) st->converged = 1;
+  }
+}
+
+// the reconstruction's results into the caller's outputs
+__global__ void recon_finish_kernel(const ReconState* st, double* direction, double* t0, double* chi2, int* iterations) {
+  if (threadIdx.x != 0) return;
+  direction[0] = st->dir[0];
+  direction[1] = st->dir[1];
+  *t0 = st->t0;
+  *chi2 = st->chi2;
+  *iterations = st->failed ? -1 : st->iterations;
 }
 
 }  // namespace aerafold
