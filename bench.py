@@ -294,6 +294,7 @@ def run_gpu(args):
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": round(el / n_e2e * 1e3, 4)}
 
     single = run_single_event(binding, synth, ctx, pid, dev, stream)
+    recon = run_reconstruction(binding, synth, ctx, pid, dev, stream)
     precision = None
     if rank == 0 and not args.no_cpu_baseline:
         precision = run_precision(binding, synth, ctx, pid, dev)
@@ -331,6 +332,7 @@ def run_gpu(args):
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,
             "single_event": single,
+            "reconstruction": recon,
             "precision_fp32": precision,
             "batched_uneven": batched,
             "serving": serving,
@@ -384,6 +386,30 @@ def run_single_event(binding, synth, ctx, pid, dev, stream, reps=200):
             "host_sync_us_p50": med(host_us), "host_buffers_us_p50": med(e2e_us),
             "host_buffers_us_p99": round(e2e_us[int(0.99 * (len(e2e_us) - 1))], 2),
             "note": "two kernels per call; latency-bound (about 0.25 MB of traffic)"}
+
+
+def run_reconstruction(binding, synth, ctx, pid, dev, stream, reps=20):
+    """The iterative loop on the 124-station event of the scan workload: device time per
+    reconstruction, iterations, and the angle between the result and the generator's true
+    direction."""
+    import math
+    import torch
+    ev = synth.direction_scan()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    tr, pos, ts = t(ev.traces), t(ev.pos_m), t(ev.t_start_ns)
+    r = ctx.reconstruct(pid, tr, pos, ts, ev.fs_hz, max_iter=8, tol_rad=1e-6, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        r = ctx.reconstruct(pid, tr, pos, ts, ev.fs_hz, max_iter=8, tol_rad=1e-6, stream=stream, sync=False)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    d = r["direction"].cpu().numpy()
+    zt, at = ev.true_dir
+    ang = math.acos(min(1.0, math.sin(d[0]) * math.sin(zt) * math.cos(d[1] - at) + math.cos(d[0]) * math.cos(zt)))
+    return {"workload": "124 stations x 2048 samples, max 8 iterations, tol 1e-6 rad",
+            "device_ms_per_reconstruction": round(a.elapsed_time(b) / reps, 4),
+            "iterations": int(r["iterations"].item()), "angle_to_true_direction_deg": round(math.degrees(ang), 4)}
 
 
 def run_precision(binding, synth, ctx, pid, dev):
