@@ -197,6 +197,24 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
 ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable);
 ar_status ar_kernel_times(ar_ctx* ctx, float* ms);
 
+/* Tensor-core DFT variant of ar_unfold: the same outputs, in the same layouts, with both
+ * transforms (the forward transform of the voltages, Sec. 4, and the inverse transform of
+ * the analytic signal, Sec. 2) computed as DFT-as-GEMM on tcgen05 tensor cores in BF16 with
+ * FP32 accumulation, on 512-sample sub-blocks: N = A x 512, and only the N/4 bins of the
+ * 30-80 MHz band enter the GEMMs (j = j1 + A j2, 128 bins per sub-block phase j1). FP32
+ * operands are split into BF16 parts: split_terms = 3 keeps hi*hi + hi*lo + lo*hi of a two-way
+ * split (about 16 significant bits per product), 6 adds the terms of a three-way split down
+ * to 2^-24 (FP32-level). Interpolation, solve, twiddles and the sub-block-phase DFTs are FP32
+ * as in ar_unfold; direction cells and timing FP64. The library keeps a workspace of about
+ * 20 B per station sample and up to 2^25 x 10 B for the pairs (processed in chunks of
+ * 2^25 / N pairs).
+ * ev, out: as ar_unfold (device memory); S * N <= 2^24.
+ * With ar_set_profiling on, ar_kernel_times gives ms[0] = forward transform and the first
+ * chunk's solve, ms[1] = the first chunk's inverse GEMM, ms[2] = the rest (post-pass, later
+ * chunks, residual).
+ * Errors: as ar_unfold, and AR_ERR_INVALID_ARG for split_terms not 3 or 6 or S * N > 2^24. */
+ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, int32_t split_terms, void* stream);
+
 /* ---- batched launches over uneven events ----
  *
  * A batch plan runs many events of different sizes (stations, trace lengths, direction

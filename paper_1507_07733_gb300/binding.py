@@ -32,7 +32,7 @@ EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
             "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy",
             "ar_server_create", "ar_submit", "ar_poll", "ar_wait", "ar_ticket_times", "ar_ticket_release",
-            "ar_server_destroy", "ar_reconstruct"]
+            "ar_server_destroy", "ar_reconstruct", "ar_unfold_tc"]
 
 
 class LibraryMissing(RuntimeError):
@@ -111,6 +111,7 @@ def load(path: str | None = None):
         L.ar_load_pattern.argtypes = [vp, ctypes.POINTER(ar_pattern_desc), vp, ctypes.POINTER(i32)]
         L.ar_prepare.argtypes = [vp, i32, dbl, i32, i32]
         L.ar_unfold.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
+        L.ar_unfold_tc.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), ctypes.c_int32, vp]
         L.ar_sync.argtypes = [vp, vp]
         L.ar_unfold_host.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
         L.ar_set_profiling.argtypes = [vp, i32]
@@ -180,6 +181,11 @@ def ar_prepare(ctx, n_samples: int, fs_hz: float, pattern_id: int, max_stations:
 
 def ar_unfold(ctx, ev: ar_event, out: ar_outputs, stream: int = 0) -> None:
     _check(ctx, load().ar_unfold(ctx, ctypes.byref(ev), ctypes.byref(out), ctypes.c_void_p(stream)))
+
+
+def ar_unfold_tc(ctx, ev: ar_event, out: ar_outputs, split_terms: int = 3, stream: int = 0) -> None:
+    _check(ctx, load().ar_unfold_tc(ctx, ctypes.byref(ev), ctypes.byref(out), int(split_terms),
+                                    ctypes.c_void_p(stream)))
 
 
 def ar_sync(ctx, stream: int = 0) -> None:
@@ -359,6 +365,22 @@ class Context:
         ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
         st = stream if stream is not None else torch.cuda.current_stream(traces.device)
         ar_unfold(self.h, ev, outputs_struct(out), st.cuda_stream)
+        if sync:
+            ar_sync(self.h, st.cuda_stream)
+        return out
+
+    def unfold_tc(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, split_terms: int = 3,
+                  fs_hz: float = 200e6, refractive_index: float = 1.0, out: dict | None = None,
+                  traces_out: bool = True, stream=None, sync: bool = False) -> dict:
+        """ar_unfold_tc: the tensor-core DFT variant (split-BF16 x3 or x6) on device tensors."""
+        import torch
+        S, _, N = traces.shape
+        D = dirs_rad.shape[0]
+        if out is None:
+            out, _ = alloc_outputs(D, S, N, device=traces.device, traces=traces_out)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        st = stream if stream is not None else torch.cuda.current_stream(traces.device)
+        ar_unfold_tc(self.h, ev, outputs_struct(out), split_terms, st.cuda_stream)
         if sync:
             ar_sync(self.h, st.cuda_stream)
         return out

@@ -23,6 +23,7 @@
 
 #include "../../include/aerafold.h"
 #include "kernels.cuh"
+#include "tc_dft.cuh"
 
 using namespace aerafold;
 
@@ -77,7 +78,13 @@ struct ar_ctx {
   // per-kernel timing
   bool profiling = false;
   bool timed = false;
+  bool timed_tc = false;   // the last timed call was ar_unfold_tc (four events)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // tensor-core DFT variant: the split DFT matrices ([0] forward, [1] inverse; 3 BF16 planes
+  // each, in the GEMM's shared-memory image) and a workspace for the GEMM operands
+  uint4* tc_b[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  unsigned char* tc_ws = nullptr;
+  size_t tc_ws_bytes = 0;
 };
 
 namespace {
@@ -401,7 +408,10 @@ ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, con
   cudaError_t e = launch_path<N_>(b, pat.desc, pat.table, ev, out, rs.k_lo, rs.kc->grid, stream,
                                   ctx->profiling ? ctx->ev : nullptr);
   if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-  if (ctx->profiling) ctx->timed = true;
+  if (ctx->profiling) {
+    ctx->timed = true;
+    ctx->timed_tc = false;
+  }
   return AR_OK;
 }
 
@@ -493,6 +503,9 @@ ar_status ar_destroy(ar_ctx* ctx) {
   cudaFree(ctx->spec);
   cudaFree(ctx->dir_done);
   cudaFree(ctx->recon);
+  for (auto& m : ctx->tc_b)
+    for (auto* p : m) cudaFree(p);
+  cudaFree(ctx->tc_ws);
   cudaFree(ctx->d_err);
   delete ctx;
   return AR_OK;
@@ -731,9 +744,195 @@ ar_status ar_kernel_times(ar_ctx* ctx, float* ms) {
   if (!ctx) return AR_ERR_INVALID_ARG;
   if (!ms || !ctx->timed) return fail(ctx, AR_ERR_INVALID_ARG, "no timed ar_unfold to report");
   AR_CUDA(ctx, cudaEventSynchronize(ctx->ev[2]));
+  if (ctx->timed_tc) {
+    AR_CUDA(ctx, cudaEventSynchronize(ctx->ev[3]));
+    AR_CUDA(ctx, cudaEventElapsedTime(&ms[0], ctx->ev[0], ctx->ev[1]));
+    AR_CUDA(ctx, cudaEventElapsedTime(&ms[1], ctx->ev[1], ctx->ev[2]));
+    AR_CUDA(ctx, cudaEventElapsedTime(&ms[2], ctx->ev[2], ctx->ev[3]));
+    return AR_OK;
+  }
   AR_CUDA(ctx, cudaEventElapsedTime(&ms[0], ctx->ev[0], ctx->ev[1]));
   AR_CUDA(ctx, cudaEventElapsedTime(&ms[1], ctx->ev[1], ctx->ev[2]));
   ms[2] = 0.0f;   // the residual runs inside the unfold kernel
+  return AR_OK;
+}
+
+}  // extern "C"
+
+// ---- tensor-core DFT variant --------------------------------------------------------------
+//
+// The forward and inverse transforms as split-BF16 GEMMs on tcgen05 tensor cores (tc_dft.cuh):
+// per call, the pre-pass and the forward GEMM over all stations, then per chunk of pairs the
+// solve, the inverse GEMM and the post-pass, then the per-direction residual.
+
+namespace {
+
+constexpr long long kTcMaxStationSamples = 1ll << 24;   // S * N: bounds the forward workspace
+constexpr long long kTcChunkSamples = 1ll << 25;        // pairs * N per inverse chunk
+
+// round to the nearest BF16 (8 significant bits, ties to even) from FP64, as BF16 bits
+uint16_t bf16_bits(double x, double* value) {
+  if (x == 0.0) {
+    *value = 0.0;
+    return 0;
+  }
+  int e = 0;
+  std::frexp(x, &e);   // |x| = m 2^e, 0.5 <= m < 1
+  const double q = std::ldexp(std::nearbyint(std::ldexp(x, 8 - e)), e - 8);
+  *value = q;
+  const float f = static_cast<float>(q);   // exact: 8 significant bits
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof u);
+  return static_cast<uint16_t>(u >> 16);
+}
+
+// The two real DFT matrices of the four-step transforms, split into three BF16 planes from
+// FP64 and laid out as the GEMM's shared-memory image. Rows are output columns, columns the
+// K index; complex values are interleaved (re, im).
+//   forward  (256 x 1024): X[j2] = sum_n2 W[n2] e^{-2 pi i j2 n2/512}
+//   inverse (1024 x 256):  Y[n2] = sum_j2 Z[j2] e^{+2 pi i j2 n2/512}
+ar_status build_tc_tables(ar_ctx* ctx) {
+  if (ctx->tc_b[0][0]) return AR_OK;
+  for (int which = 0; which < 2; ++which) {
+    const int rows = which == 0 ? tc::kFwdN : tc::kInvN;
+    const int cols = which == 0 ? tc::kFwdK : tc::kInvK;
+    const int chunks = cols / tc::kBK;
+    std::vector<uint16_t> img[3];
+    for (auto& v : img) v.assign(static_cast<size_t>(rows) * cols, 0);
+    for (int r = 0; r < rows; ++r) {
+      for (int c = 0; c < cols; ++c) {
+        const int out_bin = r >> 1, out_part = r & 1, in_bin = c >> 1, in_part = c & 1;
+        const long t = (static_cast<long>(out_bin) * in_bin) % tc::kSub;
+        const double a = 2.0 * M_PI * static_cast<double>(t) / tc::kSub;
+        const double cs = std::cos(a), sn = which == 0 ? -std::sin(a) : std::sin(a);
+        // (re, im) of the output from (re, im) of the input: [[cs, -sn], [sn, cs]]
+        const double v = out_part == 0 ? (in_part == 0 ? cs : -sn) : (in_part == 0 ? sn : cs);
+        double h, m, l;
+        const uint16_t bh = bf16_bits(v, &h);
+        const uint16_t bm = bf16_bits(v - h, &m);
+        const uint16_t bl = bf16_bits(v - h - m, &l);
+        const size_t idx = (static_cast<size_t>(r / tc::kBN) * chunks + c / tc::kBK) * (tc::kTileB / 2) +
+                           tc::core_offset(r % tc::kBN, c % tc::kBK) / 2;
+        img[0][idx] = bh;
+        img[1][idx] = bm;
+        img[2][idx] = bl;
+      }
+    }
+    for (int pl = 0; pl < 3; ++pl) {
+      const size_t bytes = img[pl].size() * sizeof(uint16_t);
+      AR_CUDA(ctx, cudaMalloc(&ctx->tc_b[which][pl], bytes));
+      AR_CUDA(ctx, cudaMemcpy(ctx->tc_b[which][pl], img[pl].data(), bytes, cudaMemcpyHostToDevice));
+    }
+  }
+  AR_CUDA(ctx, cudaFuncSetAttribute(tc::split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(tc::kGemmSmem)));
+  return AR_OK;
+}
+
+size_t pad128(size_t x) { return (x + 127) / 128 * 128; }
+
+cudaError_t launch_gemm(ar_ctx* ctx, const float* a, size_t m_pad, int which, int terms, float* d,
+                        cudaStream_t stream) {
+  tc::GemmParams gp{};
+  gp.a = a;
+  for (int pl = 0; pl < 3; ++pl) gp.b[pl] = ctx->tc_b[which][pl];
+  gp.d = d;
+  gp.err = ctx->d_err;
+  gp.k = which == 0 ? tc::kFwdK : tc::kInvK;
+  gp.n = which == 0 ? tc::kFwdN : tc::kInvN;
+  gp.terms = terms;
+  const dim3 grid(gp.n / tc::kBN, static_cast<unsigned>(m_pad / tc::kBM));
+  tc::split_gemm_kernel<<<grid, 128, tc::kGemmSmem, stream>>>(gp);
+  return cudaGetLastError();
+}
+
+template <int N_>
+cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f, long long chunk,
+                      cudaStream_t stream) {
+  constexpr int A = N_ / tc::kSub;
+  const int S = ev.n_st, D = ev.n_dir;
+  const long long pairs = static_cast<long long>(S) * D;
+  float* wf = reinterpret_cast<float*>(ctx->tc_ws);
+  float* xf = wf + rows_f * tc::kFwdK;
+  float* zr = xf + rows_f * tc::kFwdN;
+  const size_t rows_c = pad128(static_cast<size_t>(2 * A) * chunk);
+  float* yi = zr + rows_c * tc::kInvK;
+  const bool prof = ctx->profiling;
+  cudaError_t e;
+  if (prof && (e = cudaEventRecord(ctx->ev[0], stream)) != cudaSuccess) return e;
+  tc::tc_forward_pre_kernel<N_><<<2 * S, tc::kSub, 0, stream>>>(ev, reinterpret_cast<float2*>(wf));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_gemm(ctx, wf, rows_f, 0, terms, xf, stream)) != cudaSuccess) return e;
+  const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f);
+  for (long long p0 = 0; p0 < pairs; p0 += chunk) {
+    const int np = static_cast<int>(std::min(chunk, pairs - p0));
+    tc::tc_solve_kernel<N_><<<np, 256, solve_smem, stream>>>(ev, reinterpret_cast<const float2*>(xf),
+                                                             reinterpret_cast<float2*>(zr), p0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[1], stream)) != cudaSuccess) return e;
+    if ((e = launch_gemm(ctx, zr, pad128(static_cast<size_t>(2 * A) * np), 1, terms, yi, stream)) != cudaSuccess)
+      return e;
+    if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[2], stream)) != cudaSuccess) return e;
+    tc::tc_inverse_post_kernel<N_><<<np, tc::kSub, 0, stream>>>(ev, reinterpret_cast<const float2*>(yi), p0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  tc::tc_residual_kernel<<<D, 128, 0, stream>>>(ev);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (prof && (e = cudaEventRecord(ctx->ev[3], stream)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, int32_t split_terms, void* stream) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (split_terms != 3 && split_terms != 6)
+    return fail(ctx, AR_ERR_INVALID_ARG, "split_terms=%d: 3 or 6", split_terms);
+  ar_status st = check_event(ctx, ev, out);
+  if (st != AR_OK) return st;
+  const long long S = ev->n_stations, N = ev->n_samples;
+  if (N == 1024 || N == 2048 || N == 4096) {
+    if (S * N > kTcMaxStationSamples)
+      return fail(ctx, AR_ERR_INVALID_ARG, "the tensor-core variant takes at most %lld station samples (S*N=%lld)",
+                  kTcMaxStationSamples, S * N);
+  }
+  AR_CUDA(ctx, cudaSetDevice(ctx->device));
+  Resolved rs;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve_dirs(ctx, ev->n_dirs)) != AR_OK) return st;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if ((st = build_tc_tables(ctx)) != AR_OK) return st;
+  }
+  const int A = ev->n_samples / tc::kSub;
+  const long long pairs = S * ev->n_dirs;
+  const long long chunk = std::min<long long>(pairs, std::max<long long>(1, kTcChunkSamples / N));
+  const size_t rows_f = pad128(static_cast<size_t>(2 * A) * S);
+  const size_t rows_c = pad128(static_cast<size_t>(2 * A) * chunk);
+  const size_t need = sizeof(float) * (rows_f * (tc::kFwdK + tc::kFwdN) + rows_c * (tc::kInvK + tc::kInvN));
+  if (need > ctx->tc_ws_bytes) {
+    AR_CUDA(ctx, cudaDeviceSynchronize());
+    cudaFree(ctx->tc_ws);
+    ctx->tc_ws = nullptr;
+    ctx->tc_ws_bytes = 0;
+    AR_CUDA(ctx, cudaMalloc(&ctx->tc_ws, need));
+    ctx->tc_ws_bytes = need;
+  }
+  const PatternDev& pat = ctx->patterns[ev->pattern_id];
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  const EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int terms = split_terms;
+  cudaError_t e = ev->n_samples == 1024   ? launch_tc<1024>(ctx, desc, terms, rows_f, chunk, s)
+                  : ev->n_samples == 2048 ? launch_tc<2048>(ctx, desc, terms, rows_f, chunk, s)
+                                          : launch_tc<4096>(ctx, desc, terms, rows_f, chunk, s);
+  if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "tensor-core path launch failed: %s", cudaGetErrorString(e));
+  if (ctx->profiling) {
+    ctx->timed = true;
+    ctx->timed_tc = true;
+  }
   return AR_OK;
 }
 

@@ -1,0 +1,405 @@
+// tc_dft.cuh -- the transforms of the unfolding as tensor-core DFTs (sm_103a, tcgen05).
+//
+// A precision variant of the FP32 FFT path (the forward transform of Sec. 4 and the inverse
+// transform of the analytic signal, Sec. 2). Both transforms of an N-sample trace are split
+// into 512-sample sub-blocks, A = N/512 of them. Only the M = N/4 bins of the 30-80 MHz band,
+// k = k_lo + j (j < M), take part, and j = j1 + A j2 with j1 < A and j2 < M/A = 128:
+//
+//   forward   X[k_lo + j1 + A j2] = sum_n2 e^{-2 pi i j2 n2/512} W[j1][n2],
+//             W[j1][n2] = e^{-2 pi i j1 n2/N} sum_n1 x'[512 n1 + n2] e^{-2 pi i j1 n1/A},
+//             x'[n] = x[n] e^{-2 pi i k_lo n/N}
+//   inverse   z[n2 + 512 n1] = e^{2 pi i k_lo n/N} sum_j1 e^{2 pi i j1 n1/A} e^{2 pi i j1 n2/N} Y[j1][n2],
+//             Y[j1][n2] = sum_j2 Zf[k_lo + j1 + A j2] e^{2 pi i j2 n2/512}
+//
+// The 512 x 128 (forward) and 128 x 512 (inverse) complex DFT matrices are the GEMMs, one row
+// per (station, channel, j1) or (pair, polarisation, j1). Complex numbers are stored as
+// interleaved (re, im) pairs and the GEMMs are real: K = 1024, 256 output columns (forward)
+// and K = 256, 1024 output columns (inverse). The A-point DFTs over the sub-block phase and
+// the twiddles run in FP32 on the SIMT cores before (forward) and after (inverse) the GEMM.
+//
+// Precision: the GEMMs run on tensor cores in BF16 with FP32 accumulation. Each FP32 operand
+// is split into BF16 parts (x = hi + mid + lo, each the round-to-nearest of what is left) and
+// the products kept are those down to the target precision: 3 (hi*hi, hi*lo, lo*hi from a two-
+// way split) or 6 (hi*hi, hi*mid, mid*hi, hi*lo, mid*mid, lo*hi from a three-way split). The
+// DFT matrices are split on the host from FP64 values.
+//
+// Tensor-core details (PTX ISA, tcgen05): one CTA of 128 threads computes a 128 x 256 tile of
+// D = A B^T (A row-major M x K, B row-major N x K, both K-major); the accumulators (a chunk's
+// partial sum and the running sum, see below) live in 512 columns of tensor memory allocated
+// by warp 0; operands sit in shared memory in the no-swizzle K-major core-matrix layout (a
+// core matrix is 8 rows x 16 bytes; within a 64-wide K chunk, the core matrix of rows
+// 8a..8a+7 and columns 8b..8b+7 starts at byte 1024 a + 128 b: leading byte offset 128 along
+// K, stride byte offset 1024 along M or N); thread 0 issues tcgen05.mma (M 128, N 256, K 16
+// each) and commits to an mbarrier that all threads wait on (bounded) before the shared
+// memory is refilled; the threads fold the partial into the sum, and the epilogue reads the
+// sum with tcgen05.ld. B comes pre-arranged in that shared-memory image, one 32 KB block per
+// (N tile, K chunk, plane); A is FP32 and is split while it is staged.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace aerafold {
+namespace tc {
+
+constexpr int kSub = 512;                         // sub-block length
+constexpr int kBandPhase = 128;                   // band bins per sub-block phase j1 (M / A)
+constexpr int kBM = 128, kBN = 256, kBK = 64;     // CTA tile and K chunk
+constexpr unsigned kTileA = kBM * kBK * 2;        // bytes of one BF16 plane of the A tile (16 KB)
+constexpr unsigned kTileB = kBN * kBK * 2;        // bytes of one BF16 plane of the B tile (32 KB)
+constexpr int kFwdK = 2 * kSub, kFwdN = 2 * kBandPhase;   // forward GEMM: K 1024, 256 outputs
+constexpr int kInvK = 2 * kBandPhase, kInvN = 2 * kSub;   // inverse GEMM: K 256, 1024 outputs
+constexpr size_t kGemmSmem = 3 * kTileA + 3 * kTileB + 64;
+
+// byte offset of element (r, c) of a 128- or 256-row, 64-column K-major BF16 tile
+__host__ __device__ constexpr unsigned core_offset(int r, int c) {
+  return static_cast<unsigned>((r >> 3) * 1024 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kBN >> 3) << 17) |
+                            (uint32_t(kBM >> 4) << 24);
+
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading byte offset >> 4
+// (bits 16-29), stride byte offset >> 4 (bits 32-45), version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t a = smem_u32(p);
+  return ((a & 0x3FFFFull) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) | (1ull << 46);
+}
+
+// the products kept, as (plane of A, plane of B), most significant first
+__constant__ int c_terms[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+
+struct GemmParams {
+  const float* a;          // [m_pad][k] FP32, row-major
+  const uint4* b[3];       // BF16 planes of B in the shared-memory image: [n / 256][k / 64][32 KB]
+  float* d;                // [m_pad][n] FP32
+  unsigned* err;
+  int k, n, terms;         // k % 64 == 0, n % 256 == 0, terms 3 or 6
+};
+
+// FP32 -> BF16 parts, round to nearest at each step: x = hi + mid (+ lo)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);   // exact
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes: thread t gets row (32 w + t)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Accumulation. The tensor cores' FP32 accumulator loses about 2^-26 of relative precision,
+// with a bias, at every MMA (measured: the error grows linearly with the number of MMAs into
+// one accumulator), so one 64-wide K chunk is accumulated at a time into a partial region P
+// (columns 256..511 of tensor memory) and folded into the sum S (columns 0..255) by the
+// threads with IEEE round-to-nearest FP32 additions. The first chunk accumulates into S
+// directly.
+constexpr int kTmemCols = 2 * kBN;
+
+__global__ void __launch_bounds__(128, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sa = smem;                           // planes x 16 KB
+  unsigned char* sb = smem + 3 * kTileA;              // planes x 32 KB
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 3 * kTileA + 3 * kTileB);
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.y * kBM, nt = blockIdx.x;
+  const int planes = p.terms == 6 ? 3 : 2;
+  const int chunks = p.k / kBK;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(bar, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t t_sum = *taddr_s, t_part = t_sum + kBN;
+  const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;   // this warp's accumulator lanes
+
+  bool ok = true;
+  unsigned phase = 0;
+  for (int kc = 0; kc < chunks; ++kc, phase ^= 1u) {
+    // A: 128 rows x 64 columns of FP32, 8 columns (one core-matrix row) per step; rows vary
+    // fastest across threads so that each group of 8 threads stores 128 contiguous bytes
+    for (int v = tid; v < kBM * kBK / 8; v += 128) {
+      const int r = (v & 7) | ((v >> 6) << 3), c8 = (v >> 3) & 7;
+      const float4* src = reinterpret_cast<const float4*>(p.a + static_cast<size_t>(m0 + r) * p.k + kc * kBK + 8 * c8);
+      const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
+      const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) split3(xs[i], h[i], m[i], l[i]);
+      const unsigned off = core_offset(r, 8 * c8);
+      *reinterpret_cast<uint4*>(sa + off) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(sa + kTileA + off) = *reinterpret_cast<const uint4*>(m);
+      if (planes == 3) *reinterpret_cast<uint4*>(sa + 2 * kTileA + off) = *reinterpret_cast<const uint4*>(l);
+    }
+    // B: the pre-arranged image, copied as is
+    for (int pl = 0; pl < planes; ++pl) {
+      const uint4* src = p.b[pl] + (static_cast<size_t>(nt) * chunks + kc) * (kTileB / 16);
+      uint4* dst = reinterpret_cast<uint4*>(sb + pl * kTileB);
+      for (int v = tid; v < static_cast<int>(kTileB / 16); v += 128) dst[v] = __ldg(src + v);
+    }
+    fence_proxy_async_smem();   // the staged operands, visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");   // the last fold's P reads
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dst = kc == 0 ? t_sum : t_part;
+#pragma unroll 1
+      for (int ks = 0; ks < kBK / 16; ++ks) {
+#pragma unroll 1
+        for (int t = 0; t < p.terms; ++t) {
+          const uint64_t ad = smem_desc(sa + c_terms[t][0] * kTileA + ks * 256);
+          const uint64_t bd = smem_desc(sb + c_terms[t][1] * kTileB + ks * 256);
+          const unsigned acc = (ks > 0 || t > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
+              "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+              : "memory");
+        }
+      }
+      // arrives on the mbarrier once the MMAs above have completed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(bar))
+                   : "memory");
+    }
+    ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (kc > 0) {   // fold: S += P, round to nearest
+#pragma unroll 1
+      for (int c = 0; c < kBN; c += 32) {
+        uint32_t a[32], b[32];
+        tmem_ld32(t_sum + lane_base + c, a);
+        tmem_ld32(t_part + lane_base + c, b);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) a[i] = __float_as_uint(__fadd_rn(__uint_as_float(a[i]), __uint_as_float(b[i])));
+        tmem_st32(t_sum + lane_base + c, a);
+      }
+      tmem_wait_st();
+    }
+  }
+  if (ok) {
+    // warp w reads accumulator lanes 32w..32w+31 (rows of D), 32 columns at a time
+    float* drow = p.d + static_cast<size_t>(m0 + 32 * warp + (tid & 31)) * p.n + nt * kBN;
+#pragma unroll 1
+    for (int c = 0; c < kBN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(t_sum + lane_base + c, r);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(drow + c + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+                                                               __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+    }
+  } else {
+    // the MMAs never signalled completion: report, give them one more bounded wait, then
+    // release the tensor memory
+    if (tid == 0) atomicOr(p.err, kErrTmaTimeout);
+    mbar_wait_bounded(bar, phase, kWaitLimitNs);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*taddr_s), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ---- forward: phase rotation, A-point DFT over the sub-block phase, twiddle ----------------
+// One CTA per (station, channel), thread n2; writes the GEMM rows ((s * 2 + c) * A + j1) of
+// 512 interleaved complex values W[j1][n2].
+template <int N_>
+__global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_constant__ EventDesc ev, float2* w) {
+  constexpr int N = N_, A = N / kSub;
+  const int sc = blockIdx.x, n2 = threadIdx.x;
+  const float* x = ev.traces + static_cast<size_t>(sc) * N;
+  float2 y[A];
+#pragma unroll
+  for (int n1 = 0; n1 < A; ++n1) {
+    const int n = n2 + kSub * n1;
+    const float v = __ldg(x + n);
+    const float2 ph = __ldg(ev.wn + ((ev.k_lo * n) & (N - 1)));   // exp(-2 pi i k_lo n / N)
+    y[n1] = make_float2(v * ph.x, v * ph.y);
+  }
+  dft<A, -1>(y);
+#pragma unroll
+  for (int j1 = 0; j1 < A; ++j1) {
+    const float2 t = j1 == 0 ? y[0] : cmul(y[j1], __ldg(ev.wn + j1 * n2));   // exp(-2 pi i j1 n2 / N)
+    w[(static_cast<size_t>(sc) * A + j1) * kSub + n2] = t;
+  }
+}
+
+// ---- per pair: VEL interpolation and 2x2 solve (as the FP32 path) -> inverse GEMM rows ----
+// One CTA per pair of the chunk [pair0, pair0 + gridDim.x); the forward GEMM output holds
+// X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2.
+template <int N_>
+__global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ EventDesc ev, const float2* xf,
+                                                       float2* z, long long pair0) {
+  constexpr int N = N_, M = N / 4, A = N / kSub;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* hn = reinterpret_cast<float2*>(smem_raw);   // [n_f][8]: 4 values, 4 slopes
+  const int lp = blockIdx.x, tid = threadIdx.x;
+  const long long pair = pair0 + lp;
+  const int S = ev.n_st;
+  const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
+  const DirInfo di = direction_cell(ev, ev.dirs[2 * d], ev.dirs[2 * d + 1]);
+  const int n_f = ev.n_f;
+  const size_t node = static_cast<size_t>(n_f) * 4;
+  const auto bilin = [&](int x) {
+    const float2 a = __ldg(ev.table + di.slab0 * node + x), b = __ldg(ev.table + di.slab1 * node + x);
+    const float2 c = __ldg(ev.table + di.slab2 * node + x), dd = __ldg(ev.table + di.slab3 * node + x);
+    float2 h;
+    h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+    h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+    return h;
+  };
+  for (int x = tid; x < n_f * 4; x += blockDim.x) {
+    const int f = x >> 2, cp = x & 3;
+    const float2 h = bilin(x);
+    const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
+    hn[8 * f + cp] = h;
+    hn[8 * f + 4 + cp] = csub(h1, h);
+  }
+  __syncthreads();
+  const bool valid = (di.st & kStBadDir) == 0;
+  bool sing = false;
+  constexpr float kScale = 2.0f / static_cast<float>(N);
+  const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
+  const float2* x1 = x0 + A * kBandPhase;
+  float2* zt = z + static_cast<size_t>(lp * 2) * A * kBandPhase;
+  float2* zp = zt + A * kBandPhase;
+  for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
+    const int j1 = i / kBandPhase, j2 = i % kBandPhase;
+    const int j = j1 + A * j2;
+    const int2 bf = __ldg(ev.binf + j);
+    float2 et = make_float2(0.f, 0.f), ep = et;
+    if (bf.x >= 0 && valid) {
+      const float tf = __int_as_float(bf.y);
+      const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
+      const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
+      const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));
+      const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));
+      const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));
+      const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));
+      const float2 v0 = x0[i], v1 = x1[i];
+      const float2 det = csub(cmul(a, dd), cmul(b, c));
+      const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
+      const float dd2 = cabs2(det);
+      if (dd2 > 1e-12f * sc * sc) {
+        const float inv = kScale * rcp_approx(dd2);
+        const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
+        const float2 np = csub(cmul(a, v1), cmul(c, v0));
+        const float2 ct = cmulc(nt, det), cpp = cmulc(np, det);
+        et = make_float2(ct.x * inv, ct.y * inv);
+        ep = make_float2(cpp.x * inv, cpp.y * inv);
+      } else {
+        sing = true;
+      }
+    }
+    zt[i] = et;
+    zp[i] = ep;
+  }
+  const bool any = __syncthreads_or(sing);
+  if (tid == 0) ev.status[pair] = di.st | (any ? kStSingular : 0u);
+}
+
+// ---- inverse: twiddle, A-point DFT over the sub-block phase, band phase, envelope, peak ----
+// One CTA per pair of the chunk, thread n2; the inverse GEMM output holds Y[j1][n2] at row
+// ((lp * 2 + pol) * A + j1), complex column n2.
+template <int N_>
+__global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_constant__ EventDesc ev,
+                                                               const float2* y_in, long long pair0) {
+  constexpr int N = N_, A = N / kSub;
+  const int lp = blockIdx.x, n2 = threadIdx.x;
+  const long long pair = pair0 + lp;
+  const int s = static_cast<int>(pair % ev.n_st);
+  float pw[A];
+#pragma unroll
+  for (int i = 0; i < A; ++i) pw[i] = 0.f;
+#pragma unroll
+  for (int pol = 0; pol < 2; ++pol) {
+    float2 y[A];
+    const float2* rows = y_in + static_cast<size_t>(lp * 2 + pol) * A * kSub;
+#pragma unroll
+    for (int j1 = 0; j1 < A; ++j1) {
+      const float2 v = rows[j1 * kSub + n2];
+      y[j1] = j1 == 0 ? v : cmulc(v, __ldg(ev.wn + j1 * n2));   // exp(+2 pi i j1 n2 / N)
+    }
+    dft<A, +1>(y);
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) {
+      const int n = n2 + kSub * n1;
+      const float2 zz = cmulc(y[n1], __ldg(ev.wn + ((ev.k_lo * n) & (N - 1))));   // exp(+2 pi i k_lo n / N)
+      if (ev.efield) ev.efield[(static_cast<size_t>(pair) * 2 + pol) * N + n] = zz.x;
+      pw[n1] += cabs2(zz);
+    }
+  }
+  float bv = -1.f;
+  int bi = 0;
+#pragma unroll
+  for (int n1 = 0; n1 < A; ++n1) {
+    const int n = n2 + kSub * n1;
+    const float v = sqrtf(pw[n1]);
+    if (ev.envelope) ev.envelope[static_cast<size_t>(pair) * N + n] = v;
+    if (v > bv) { bv = v; bi = n; }
+  }
+  __shared__ float rv[kSub / 32];
+  __shared__ int ri[kSub / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  if ((n2 & 31) == 0) { rv[n2 >> 5] = bv; ri[n2 >> 5] = bi; }
+  __syncthreads();
+  if (n2 == 0) {
+    for (int w = 1; w < kSub / 32; ++w)
+      if (rv[w] > bv || (rv[w] == bv && ri[w] < bi)) { bv = rv[w]; bi = ri[w]; }
+    if (bv < 0.f) { bv = 0.f; bi = 0; }
+    ev.peak_idx[pair] = bi;
+    ev.peak_amp[pair] = bv;
+    ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+  }
+}
+
+// ---- per direction: the FP64 plane-wave timing residual ------------------------------------
+__global__ void __launch_bounds__(128) tc_residual_kernel(const __grid_constant__ EventDesc ev) {
+  __shared__ double red[128 / 32];
+  direction_residual<128>(ev, blockIdx.x, red);
+}
+
+}  // namespace tc
+}  // namespace aerafold
