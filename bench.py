@@ -297,7 +297,8 @@ def run_gpu(args):
     recon = run_reconstruction(binding, synth, ctx, pid, dev, stream)
     precision = None
     if rank == 0 and not args.no_cpu_baseline:
-        precision = run_precision(binding, synth, ctx, pid, dev)
+        precision = run_precision(binding, synth, ctx, pid, dev, stream)
+    tensor_core = run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks)
 
     batched = None
     if not args.no_batch:
@@ -333,7 +334,8 @@ def run_gpu(args):
             "e2e": e2e,
             "single_event": single,
             "reconstruction": recon,
-            "precision_fp32": precision,
+            "precision": precision,
+            "tensor_core_variant": tensor_core,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -412,31 +414,94 @@ def run_reconstruction(binding, synth, ctx, pid, dev, stream, reps=20):
             "iterations": int(r["iterations"].item()), "angle_to_true_direction_deg": round(math.degrees(ang), 4)}
 
 
-def run_precision(binding, synth, ctx, pid, dev):
-    """FP32 path against the FP64 oracle on the single event at 4096 samples (and 2048):
-    relative L2 error per pair of the E-field and envelope, peak-index agreement."""
+def _pair_errors(g, ref, n):
+    def rel(a, b, m):
+        a = np.asarray(a, np.float64).reshape(-1, m)
+        b = np.asarray(b, np.float64).reshape(-1, m)
+        return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    ef = rel(g["efield"], ref["efield"], 2 * n)
+    en = rel(g["envelope"], ref["envelope"], n)
+    pa = np.abs(g["peak_amp"].astype(np.float64) - ref["peak_amp"]) / ref["peak_amp"]
+    return {"efield_rel_l2_max": float(ef.max()), "efield_rel_l2_median": float(np.median(ef)),
+            "envelope_rel_l2_max": float(en.max()), "peak_amp_rel_max": float(pa.max()),
+            "peak_idx_equal": int((g["peak_idx"] == ref["peak_idx"]).sum()), "pairs": int(ef.size),
+            "residual_abs_max_ns": float(np.abs(g["residual_ns"] - ref["residual_ns"]).max()),
+            "chi2_rel": float(np.abs(g["chi2"] - ref["chi2"]).max() / max(float(np.abs(ref["chi2"]).max()), 1.0))}
+
+
+def run_precision(binding, synth, ctx, pid, dev, stream, reps=50):
+    """Precision workload: the single event (10 stations, 1 direction) at 4096 samples
+    through the FP32 FFT path and the tensor-core split-BF16 DFT variant (x3, x6), each
+    output's error against the FP64 oracle and the device time per call; the FP32 path at
+    2048 samples as well."""
     import torch
     import oracle
     pat = synth.make_pattern()
-    res = {}
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    res = {"workload": "single event: 10 stations x 4096 samples, 1 direction (30, 45 deg)"}
     for n in (4096, 2048):
         ev = synth.single_event(n)
-        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-        out = ctx.unfold(pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad), ev.fs_hz, sync=True)
+        args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
         ref = oracle.unfold_event(pat, ev)
-        g = {k: v.cpu().numpy() for k, v in out.items()}
+        variants = [("fp32_fft", lambda: ctx.unfold(*args, ev.fs_hz, stream=stream))]
+        if n == 4096:
+            variants += [("tc_split_bf16_x3", lambda: ctx.unfold_tc(*args, split_terms=3, fs_hz=ev.fs_hz, stream=stream)),
+                         ("tc_split_bf16_x6", lambda: ctx.unfold_tc(*args, split_terms=6, fs_hz=ev.fs_hz, stream=stream))]
+        for name, fn in variants:
+            out = fn()
+            ctx.sync(stream)
+            row = _pair_errors({k: v.cpu().numpy() for k, v in out.items()}, ref, n)
+            if n == 4096:
+                for _ in range(5):
+                    fn()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    fn()
+                b.record(stream)
+                ctx.sync(stream)
+                row["device_ms_per_call"] = round(a.elapsed_time(b) / reps, 4)
+                res[name] = row
+            else:
+                res[name + "_2048"] = row
+    return res
 
-        def rel(a, b, m):
-            a = a.astype(np.float64).reshape(-1, m)
-            b = b.reshape(-1, m)
-            return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
-        ef = rel(g["efield"], ref["efield"], 2 * n)
-        en = rel(g["envelope"], ref["envelope"], n)
-        res[str(n)] = {"efield_rel_l2_max": float(ef.max()), "efield_rel_l2_median": float(np.median(ef)),
-                       "envelope_rel_l2_max": float(en.max()),
-                       "peak_idx_equal": int((g["peak_idx"] == ref["peak_idx"]).sum()),
-                       "pairs": int(ef.size),
-                       "residual_abs_max_ns": float(np.abs(g["residual_ns"] - ref["residual_ns"]).max())}
+
+def run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks, reps=20):
+    """Throughput of the tensor-core variant on the scan workload (124 stations x 64
+    directions x 2048 samples): unfolds/s per call, and the inverse GEMM's tensor rate
+    (split products counted: 2 x rows x K x 1024 x terms, rows = 2 x pairs x 4) against the
+    measured dense BF16 peak."""
+    import torch
+    ev = synth.direction_scan()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+    pairs = ev.n_stations * ev.n_dirs
+    A = ev.n_samples // 512
+    out, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev)
+    res = {"workload": "124 stations x 64 directions x 2048 samples"}
+    peak = peaks.get("bf16_tflops")
+    for terms in (3, 6):
+        fn = lambda: ctx.unfold_tc(*args, split_terms=terms, fs_hz=ev.fs_hz, out=out, stream=stream)
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        ctx.sync(stream)
+        ms = a.elapsed_time(b) / reps
+        binding.ar_set_profiling(ctx.h, 1)
+        fn()
+        ctx.sync(stream)
+        kt = binding.ar_kernel_times(ctx.h)
+        binding.ar_set_profiling(ctx.h, 0)
+        flops = 2.0 * (2 * pairs * A) * 256 * 1024 * terms
+        tflops = flops / (kt[1] * 1e-3) / 1e12
+        res[f"x{terms}"] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4),
+                            "inverse_gemm_ms": round(kt[1], 4), "inverse_gemm_tflops": round(tflops, 1),
+                            "inverse_gemm_frac_of_measured_bf16": round(tflops / peak, 4) if peak else None}
     return res
 
 
