@@ -796,7 +796,6 @@ ar_status build_tc_tables(ar_ctx* ctx) {
   for (int which = 0; which < 2; ++which) {
     const int rows = which == 0 ? tc::kFwdN : tc::kInvN;
     const int cols = which == 0 ? tc::kFwdK : tc::kInvK;
-    const int chunks = cols / tc::kBK;
     std::vector<uint16_t> img[3];
     for (auto& v : img) v.assign(static_cast<size_t>(rows) * cols, 0);
     for (int r = 0; r < rows; ++r) {
@@ -811,8 +810,7 @@ ar_status build_tc_tables(ar_ctx* ctx) {
         const uint16_t bh = bf16_bits(v, &h);
         const uint16_t bm = bf16_bits(v - h, &m);
         const uint16_t bl = bf16_bits(v - h - m, &l);
-        const size_t idx = (static_cast<size_t>(r / tc::kBN) * chunks + c / tc::kBK) * (tc::kTileB / 2) +
-                           tc::core_offset(r % tc::kBN, c % tc::kBK) / 2;
+        const size_t idx = tc::image_offset(r, c, cols);
         img[0][idx] = bh;
         img[1][idx] = bm;
         img[2][idx] = bl;
@@ -830,19 +828,65 @@ ar_status build_tc_tables(ar_ctx* ctx) {
 }
 
 size_t pad128(size_t x) { return (x + 127) / 128 * 128; }
+size_t pad256b(size_t bytes) { return (bytes + 255) / 256 * 256; }
 
-cudaError_t launch_gemm(ar_ctx* ctx, const float* a, size_t m_pad, int which, int terms, float* d,
-                        cudaStream_t stream) {
+// Workspace of one call: the two GEMMs' A images (BF16, up to 3 planes), their FP32 outputs,
+// and the split-K partial results.
+struct TcWorkspace {
+  __nv_bfloat16* fa[3];   // forward A image: rows_f x 1024
+  float* xf;              // forward D: rows_f x 256
+  __nv_bfloat16* za[3];   // inverse A image: rows_c x 256
+  float* yi;              // inverse D: rows_c x 1024
+  float* part;            // split-K partials: 2 x 128 x 128 floats per CTA of the grid
+  size_t bytes;
+};
+
+TcWorkspace tc_layout(unsigned char* base, size_t rows_f, size_t rows_c, int num_sms) {
+  TcWorkspace w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base ? base + off : nullptr;
+    off += pad256b(bytes);
+    return p;
+  };
+  for (auto& x : w.fa) x = reinterpret_cast<__nv_bfloat16*>(take(rows_f * tc::kFwdK * 2));
+  w.xf = reinterpret_cast<float*>(take(rows_f * tc::kFwdN * 4));
+  for (auto& x : w.za) x = reinterpret_cast<__nv_bfloat16*>(take(rows_c * tc::kInvK * 2));
+  w.yi = reinterpret_cast<float*>(take(rows_c * tc::kInvN * 4));
+  w.part = reinterpret_cast<float*>(take(static_cast<size_t>(2 * num_sms) * tc::kBM * tc::kBN * 4));
+  w.bytes = off;
+  return w;
+}
+
+// D (m_pad x n) = A (m_pad x K, image planes) B^T on the tensor cores. When the grid of output
+// tiles is small, K is split into groups whose folded partial sums a second kernel adds in
+// group order.
+cudaError_t launch_gemm(ar_ctx* ctx, __nv_bfloat16* const (&a)[3], size_t m_pad, int which, int terms, float* d,
+                        float* part, cudaStream_t stream) {
   tc::GemmParams gp{};
-  gp.a = a;
-  for (int pl = 0; pl < 3; ++pl) gp.b[pl] = ctx->tc_b[which][pl];
-  gp.d = d;
+  const int k = which == 0 ? tc::kFwdK : tc::kInvK;
+  const int n = which == 0 ? tc::kFwdN : tc::kInvN;
+  for (int pl = 0; pl < 3; ++pl) {
+    gp.a[pl] = reinterpret_cast<const uint4*>(a[pl]);
+    gp.b[pl] = ctx->tc_b[which][pl];
+  }
   gp.err = ctx->d_err;
-  gp.k = which == 0 ? tc::kFwdK : tc::kInvK;
-  gp.n = which == 0 ? tc::kFwdN : tc::kInvN;
+  gp.ldd = n;
+  gp.chunks = k / tc::kBK;
   gp.terms = terms;
-  const dim3 grid(gp.n / tc::kBN, static_cast<unsigned>(m_pad / tc::kBM));
-  tc::split_gemm_kernel<<<grid, 128, tc::kGemmSmem, stream>>>(gp);
+  const int tiles = static_cast<int>(m_pad / tc::kBM) * (n / tc::kBN);
+  int groups = 1;
+  while (groups * 2 <= gp.chunks && tiles * groups * 2 <= 2 * ctx->num_sms) groups *= 2;
+  gp.chunks_per_group = gp.chunks / groups;
+  gp.d = groups > 1 ? part : d;
+  gp.d_group = m_pad * static_cast<size_t>(n);
+  const dim3 grid(n / tc::kBN, static_cast<unsigned>(m_pad / tc::kBM), groups);
+  tc::split_gemm_kernel<<<grid, tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || groups == 1) return e;
+  const size_t n4 = gp.d_group / 4;
+  tc::tc_reduce_kernel<<<2 * ctx->num_sms, 256, 0, stream>>>(reinterpret_cast<const float4*>(part),
+                                                              reinterpret_cast<float4*>(d), n4, n4, groups);
   return cudaGetLastError();
 }
 
@@ -852,28 +896,28 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   constexpr int A = N_ / tc::kSub;
   const int S = ev.n_st, D = ev.n_dir;
   const long long pairs = static_cast<long long>(S) * D;
-  float* wf = reinterpret_cast<float*>(ctx->tc_ws);
-  float* xf = wf + rows_f * tc::kFwdK;
-  float* zr = xf + rows_f * tc::kFwdN;
   const size_t rows_c = pad128(static_cast<size_t>(2 * A) * chunk);
-  float* yi = zr + rows_c * tc::kInvK;
+  const TcWorkspace w = tc_layout(ctx->tc_ws, rows_f, rows_c, ctx->num_sms);
+  const int planes = terms == 6 ? 3 : 2;
+  const tc::SplitImage fimg{{w.fa[0], w.fa[1], w.fa[2]}, planes};
+  const tc::SplitImage zimg{{w.za[0], w.za[1], w.za[2]}, planes};
   const bool prof = ctx->profiling;
   cudaError_t e;
   if (prof && (e = cudaEventRecord(ctx->ev[0], stream)) != cudaSuccess) return e;
-  tc::tc_forward_pre_kernel<N_><<<2 * S, tc::kSub, 0, stream>>>(ev, reinterpret_cast<float2*>(wf));
+  tc::tc_forward_pre_kernel<N_><<<2 * S, tc::kSub, 0, stream>>>(ev, fimg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_gemm(ctx, wf, rows_f, 0, terms, xf, stream)) != cudaSuccess) return e;
+  if ((e = launch_gemm(ctx, w.fa, rows_f, 0, terms, w.xf, w.part, stream)) != cudaSuccess) return e;
   const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
-    tc::tc_solve_kernel<N_><<<np, 256, solve_smem, stream>>>(ev, reinterpret_cast<const float2*>(xf),
-                                                             reinterpret_cast<float2*>(zr), p0);
+    tc::tc_solve_kernel<N_><<<np, 256, solve_smem, stream>>>(ev, reinterpret_cast<const float2*>(w.xf), zimg, p0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[1], stream)) != cudaSuccess) return e;
-    if ((e = launch_gemm(ctx, zr, pad128(static_cast<size_t>(2 * A) * np), 1, terms, yi, stream)) != cudaSuccess)
+    if ((e = launch_gemm(ctx, w.za, pad128(static_cast<size_t>(2 * A) * np), 1, terms, w.yi, w.part, stream)) !=
+        cudaSuccess)
       return e;
     if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[2], stream)) != cudaSuccess) return e;
-    tc::tc_inverse_post_kernel<N_><<<np, tc::kSub, 0, stream>>>(ev, reinterpret_cast<const float2*>(yi), p0);
+    tc::tc_inverse_post_kernel<N_><<<np, tc::kSub, 0, stream>>>(ev, reinterpret_cast<const float2*>(w.yi), p0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   tc::tc_residual_kernel<<<D, 128, 0, stream>>>(ev);
@@ -911,7 +955,7 @@ ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, i
   const long long chunk = std::min<long long>(pairs, std::max<long long>(1, kTcChunkSamples / N));
   const size_t rows_f = pad128(static_cast<size_t>(2 * A) * S);
   const size_t rows_c = pad128(static_cast<size_t>(2 * A) * chunk);
-  const size_t need = sizeof(float) * (rows_f * (tc::kFwdK + tc::kFwdN) + rows_c * (tc::kInvK + tc::kInvN));
+  const size_t need = tc_layout(nullptr, rows_f, rows_c, ctx->num_sms).bytes;
   if (need > ctx->tc_ws_bytes) {
     AR_CUDA(ctx, cudaDeviceSynchronize());
     cudaFree(ctx->tc_ws);

@@ -23,17 +23,19 @@
 // way split) or 6 (hi*hi, hi*mid, mid*hi, hi*lo, mid*mid, lo*hi from a three-way split). The
 // DFT matrices are split on the host from FP64 values.
 //
-// Tensor-core details (PTX ISA, tcgen05): one CTA of 128 threads computes a 128 x 256 tile of
-// D = A B^T (A row-major M x K, B row-major N x K, both K-major); the accumulators (a chunk's
-// partial sum and the running sum, see below) live in 512 columns of tensor memory allocated
-// by warp 0; operands sit in shared memory in the no-swizzle K-major core-matrix layout (a
-// core matrix is 8 rows x 16 bytes; within a 64-wide K chunk, the core matrix of rows
-// 8a..8a+7 and columns 8b..8b+7 starts at byte 1024 a + 128 b: leading byte offset 128 along
-// K, stride byte offset 1024 along M or N); thread 0 issues tcgen05.mma (M 128, N 256, K 16
-// each) and commits to an mbarrier that all threads wait on (bounded) before the shared
-// memory is refilled; the threads fold the partial into the sum, and the epilogue reads the
-// sum with tcgen05.ld. B comes pre-arranged in that shared-memory image, one 32 KB block per
-// (N tile, K chunk, plane); A is FP32 and is split while it is staged.
+// Tensor-core details (PTX ISA, tcgen05). A CTA computes a 128 x 128 tile of D = A B^T (A
+// row-major M x K, B row-major N x K, both K-major) over a range of 64-wide K chunks, with 6
+// warps in three roles: warp 4 stages each chunk's operands with bulk copies into one of two
+// shared-memory stages (mbarrier full/empty pairs), warp 5 issues the tcgen05.mma
+// instructions (M 128, N 128, K 16; one per split product and K step) into tensor memory,
+// and warps 0-3 read the chunk's partial sum out of tensor memory (tcgen05.ld) and fold it
+// into the running sum (see the accumulation note below), writing the result at the end.
+// Every wait is bounded. Operands come pre-split and pre-arranged in the shared-memory image
+// of the no-swizzle K-major core-matrix layout: a core matrix is 8 rows x 16 bytes; in a
+// 128-row, 64-column block the core matrix of rows 8a..8a+7 and columns 8b..8b+7 starts at
+// byte 1024 a + 128 b (leading byte offset 128 along K, stride byte offset 1024 along M or N);
+// one 16 KB block per (row tile, K chunk, plane), so a stage is filled by plain 1-D bulk
+// copies. The producers of A (the forward pre-pass and the solve) write this image directly.
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -45,16 +47,22 @@ namespace tc {
 
 constexpr int kSub = 512;                         // sub-block length
 constexpr int kBandPhase = 128;                   // band bins per sub-block phase j1 (M / A)
-constexpr int kBM = 128, kBN = 256, kBK = 64;     // CTA tile and K chunk
-constexpr unsigned kTileA = kBM * kBK * 2;        // bytes of one BF16 plane of the A tile (16 KB)
-constexpr unsigned kTileB = kBN * kBK * 2;        // bytes of one BF16 plane of the B tile (32 KB)
+constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile and K chunk
+constexpr unsigned kBlk = kBM * kBK * 2;          // bytes of one BF16 plane of a 128 x 64 block (16 KB)
+constexpr unsigned kStageBytes = 6 * kBlk;        // A and B, up to 3 planes each
+constexpr int kStages = 2;
 constexpr int kFwdK = 2 * kSub, kFwdN = 2 * kBandPhase;   // forward GEMM: K 1024, 256 outputs
 constexpr int kInvK = 2 * kBandPhase, kInvN = 2 * kSub;   // inverse GEMM: K 256, 1024 outputs
-constexpr size_t kGemmSmem = 3 * kTileA + 3 * kTileB + 64;
+constexpr size_t kGemmSmem = kStages * kStageBytes + 256;
+constexpr int kGemmThreads = 192;
 
-// byte offset of element (r, c) of a 128- or 256-row, 64-column K-major BF16 tile
+// byte offset of element (r, c) inside a 128-row, 64-column K-major BF16 block
 __host__ __device__ constexpr unsigned core_offset(int r, int c) {
   return static_cast<unsigned>((r >> 3) * 1024 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+// BF16 element offset of (row, k) in an image of rows x k (blocks [row / 128][k / 64])
+__host__ __device__ constexpr size_t image_offset(int row, int k, int k_total) {
+  return (static_cast<size_t>(row >> 7) * (k_total >> 6) + (k >> 6)) * (kBlk / 2) + core_offset(row & 127, k & 63) / 2;
 }
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
@@ -73,11 +81,12 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
 __constant__ int c_terms[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
 
 struct GemmParams {
-  const float* a;          // [m_pad][k] FP32, row-major
-  const uint4* b[3];       // BF16 planes of B in the shared-memory image: [n / 256][k / 64][32 KB]
-  float* d;                // [m_pad][n] FP32
+  const uint4* a[3];       // BF16 planes of A, image [m_tiles][chunks] of 16 KB blocks
+  const uint4* b[3];       // BF16 planes of B, image [n_tiles][chunks] of 16 KB blocks
+  float* d;                // D, row-major with row stride ldd; split-K group g at d + g * d_group
+  size_t d_group;
   unsigned* err;
-  int k, n, terms;         // k % 64 == 0, n % 256 == 0, terms 3 or 6
+  int ldd, chunks, chunks_per_group, terms;   // terms 3 or 6
 };
 
 // FP32 -> BF16 parts, round to nearest at each step: x = hi + mid (+ lo)
@@ -86,6 +95,16 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
   const float r1 = x - __bfloat162float(h);   // exact
   m = __float2bfloat16_rn(r1);
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// store complex value z at image element (row, 2 j) .. (row, 2 j + 1) of every plane
+__device__ __forceinline__ void put_split(__nv_bfloat16* const (&img)[3], int planes, size_t off, float2 z) {
+  __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+  split3(z.x, h0, m0, l0);
+  split3(z.y, h1, m1, l1);
+  *reinterpret_cast<__nv_bfloat162*>(img[0] + off) = __halves2bfloat162(h0, h1);
+  *reinterpret_cast<__nv_bfloat162*>(img[1] + off) = __halves2bfloat162(m0, m1);
+  if (planes == 3) *reinterpret_cast<__nv_bfloat162*>(img[2] + off) = __halves2bfloat162(l0, l1);
 }
 
 // 32 consecutive accumulator columns of this warp's 32 lanes: thread t gets row (32 w + t)
@@ -111,25 +130,38 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// arrives on the mbarrier once every tcgen05.mma this thread issued before it has completed
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
 
 // Accumulation. The tensor cores' FP32 accumulator loses about 2^-26 of relative precision,
 // with a bias, at every MMA (measured: the error grows linearly with the number of MMAs into
-// one accumulator), so one 64-wide K chunk is accumulated at a time into a partial region P
-// (columns 256..511 of tensor memory) and folded into the sum S (columns 0..255) by the
-// threads with IEEE round-to-nearest FP32 additions. The first chunk accumulates into S
-// directly.
-constexpr int kTmemCols = 2 * kBN;
+// one accumulator), so each 64-wide K chunk is accumulated on its own into a partial region
+// P[chunk % 2] of tensor memory, and warps 0-3 fold it into the running sum S with IEEE
+// round-to-nearest FP32 additions, in chunk order: S = (((P0 + P1) + P2) + ...). With two
+// partial regions the MMAs of one chunk overlap the fold of the previous one.
+constexpr int kTmemCols = 512;   // S, P0, P1: 128 columns each, rounded up to a power of two
 
-__global__ void __launch_bounds__(128, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
+__global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sa = smem;                           // planes x 16 KB
-  unsigned char* sb = smem + 3 * kTileA;              // planes x 32 KB
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 3 * kTileA + 3 * kTileB);
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int m0 = blockIdx.y * kBM, nt = blockIdx.x;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* full = bars;          // [2] stage filled (bulk copies complete)
+  uint64_t* empty = bars + 2;     // [2] stage consumed (its MMAs complete)
+  uint64_t* ready = bars + 4;     // [2] partial region holds a finished chunk
+  uint64_t* pfree = bars + 6;     // [2] partial region folded (4 arrivals, one per fold warp)
+  uint64_t* done = bars + 8;      // every MMA complete
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 9);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y, g = blockIdx.z;
+  const int kc0 = g * p.chunks_per_group, nk = p.chunks_per_group;
   const int planes = p.terms == 6 ? 3 : 2;
-  const int chunks = p.k / kBK;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
@@ -137,111 +169,139 @@ __global__ void __launch_bounds__(128, 1) split_gemm_kernel(const __grid_constan
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init(bar, 1);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t t_sum = *taddr_s, t_part = t_sum + kBN;
-  const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;   // this warp's accumulator lanes
-
-  bool ok = true;
-  unsigned phase = 0;
-  for (int kc = 0; kc < chunks; ++kc, phase ^= 1u) {
-    // A: 128 rows x 64 columns of FP32, 8 columns (one core-matrix row) per step; rows vary
-    // fastest across threads so that each group of 8 threads stores 128 contiguous bytes
-    for (int v = tid; v < kBM * kBK / 8; v += 128) {
-      const int r = (v & 7) | ((v >> 6) << 3), c8 = (v >> 3) & 7;
-      const float4* src = reinterpret_cast<const float4*>(p.a + static_cast<size_t>(m0 + r) * p.k + kc * kBK + 8 * c8);
-      const float4 x0 = __ldg(src), x1 = __ldg(src + 1);
-      const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-      __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) split3(xs[i], h[i], m[i], l[i]);
-      const unsigned off = core_offset(r, 8 * c8);
-      *reinterpret_cast<uint4*>(sa + off) = *reinterpret_cast<const uint4*>(h);
-      *reinterpret_cast<uint4*>(sa + kTileA + off) = *reinterpret_cast<const uint4*>(m);
-      if (planes == 3) *reinterpret_cast<uint4*>(sa + 2 * kTileA + off) = *reinterpret_cast<const uint4*>(l);
-    }
-    // B: the pre-arranged image, copied as is
-    for (int pl = 0; pl < planes; ++pl) {
-      const uint4* src = p.b[pl] + (static_cast<size_t>(nt) * chunks + kc) * (kTileB / 16);
-      uint4* dst = reinterpret_cast<uint4*>(sb + pl * kTileB);
-      for (int v = tid; v < static_cast<int>(kTileB / 16); v += 128) dst[v] = __ldg(src + v);
-    }
-    fence_proxy_async_smem();   // the staged operands, visible to the tensor cores
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");   // the last fold's P reads
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dst = kc == 0 ? t_sum : t_part;
-#pragma unroll 1
-      for (int ks = 0; ks < kBK / 16; ++ks) {
-#pragma unroll 1
-        for (int t = 0; t < p.terms; ++t) {
-          const uint64_t ad = smem_desc(sa + c_terms[t][0] * kTileA + ks * 256);
-          const uint64_t bd = smem_desc(sb + c_terms[t][1] * kTileB + ks * 256);
-          const unsigned acc = (ks > 0 || t > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
-              "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-              : "memory");
-        }
-      }
-      // arrives on the mbarrier once the MMAs above have completed
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(bar))
-                   : "memory");
-    }
-    ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
-    if (__syncthreads_or(!ok)) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (kc > 0) {   // fold: S += P, round to nearest
-#pragma unroll 1
-      for (int c = 0; c < kBN; c += 32) {
-        uint32_t a[32], b[32];
-        tmem_ld32(t_sum + lane_base + c, a);
-        tmem_ld32(t_part + lane_base + c, b);
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) a[i] = __float_as_uint(__fadd_rn(__uint_as_float(a[i]), __uint_as_float(b[i])));
-        tmem_st32(t_sum + lane_base + c, a);
-      }
-      tmem_wait_st();
-    }
+  if (tid == 32) {
+    for (int i = 0; i < 9; ++i) mbar_init(bars + i, (i == 6 || i == 7) ? 4 : 1);
   }
-  if (ok) {
-    // warp w reads accumulator lanes 32w..32w+31 (rows of D), 32 columns at a time
-    float* drow = p.d + static_cast<size_t>(m0 + 32 * warp + (tid & 31)) * p.n + nt * kBN;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t t_sum = *taddr_s;
+  bool ok = true;
+
+  if (warp == 4) {
+    // ---- producer: bulk copies of each chunk's A and B blocks into a free stage ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i & 1;
+        if (i >= 2) ok = mbar_wait_bounded(&empty[s], ((i >> 1) - 1) & 1, kWaitLimitNs);
+        if (!ok) break;
+        unsigned char* st = smem + s * kStageBytes;
+        mbar_arrive_expect_tx(&full[s], 2u * planes * kBlk);
+        for (int pl = 0; pl < planes; ++pl) {
+          tma_bulk_g2s(st + pl * kBlk, p.a[pl] + (static_cast<size_t>(mt) * p.chunks + kc0 + i) * (kBlk / 16), kBlk,
+                       &full[s]);
+          tma_bulk_g2s(st + (3 + pl) * kBlk, p.b[pl] + (static_cast<size_t>(nt) * p.chunks + kc0 + i) * (kBlk / 16),
+                       kBlk, &full[s]);
+        }
+        issued = i + 1;
+      }
+      if (!ok) atomicOr(p.err, kErrTmaTimeout);
+      // no copy may still be landing when the CTA leaves: wait (bounded) for the last ones
+      for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+        mbar_wait_bounded(&full[i & 1], (i >> 1) & 1, kWaitLimitNs);
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i & 1;
+        ok = mbar_wait_bounded(&full[s], (i >> 1) & 1, kWaitLimitNs);
+        if (ok && i >= 2) ok = mbar_wait_bounded(&pfree[s], ((i >> 1) - 1) & 1, kWaitLimitNs);
+        if (!ok) break;
+        tc_fence_after();
+        const unsigned char* st = smem + s * kStageBytes;
+        const uint32_t dst = t_sum + kBN * (1 + s);
 #pragma unroll 1
-    for (int c = 0; c < kBN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(t_sum + lane_base + c, r);
-      tmem_wait_ld();
-#pragma unroll
-      for (int i = 0; i < 32; i += 4)
-        *reinterpret_cast<float4*>(drow + c + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
-                                                               __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+        for (int ks = 0; ks < kBK / 16; ++ks) {
+#pragma unroll 1
+          for (int t = 0; t < p.terms; ++t) {
+            const uint64_t ad = smem_desc(st + c_terms[t][0] * kBlk + ks * 256);
+            const uint64_t bd = smem_desc(st + (3 + c_terms[t][1]) * kBlk + ks * 256);
+            const unsigned acc = (ks > 0 || t > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                : "memory");
+          }
+        }
+        tc_commit(&empty[s]);   // the stage may be refilled
+        tc_commit(&ready[s]);   // the partial region may be folded
+      }
+      if (!ok) atomicOr(p.err, kErrTmaTimeout);
+      tc_commit(done);
+      mbar_wait_bounded(done, 0, kWaitLimitNs);   // no MMA outlives the tensor memory
     }
   } else {
-    // the MMAs never signalled completion: report, give them one more bounded wait, then
-    // release the tensor memory
-    if (tid == 0) atomicOr(p.err, kErrTmaTimeout);
-    mbar_wait_bounded(bar, phase, kWaitLimitNs);
+    // ---- fold warps: S = S + P[chunk % 2]; the last chunk's sum goes to global memory ----
+    const uint32_t lanes = static_cast<uint32_t>(32 * warp) << 16;
+    float* drow = p.d + g * p.d_group + static_cast<size_t>(mt * kBM + 32 * warp + lane) * p.ldd + nt * kBN;
+    for (int i = 0; i < nk; ++i) {
+      const int b = i & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ready[b], (i >> 1) & 1, kWaitLimitNs));   // warp-uniform
+      if (!ok) break;
+      tc_fence_after();
+      const bool last = i == nk - 1;
+#pragma unroll 1
+      for (int c = 0; c < kBN; c += 32) {
+        uint32_t x[32], y[32];
+        tmem_ld32(t_sum + kBN * (1 + b) + lanes + c, x);
+        if (i > 0) tmem_ld32(t_sum + lanes + c, y);
+        tmem_wait_ld();
+        if (i > 0) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) x[k] = __float_as_uint(__fadd_rn(__uint_as_float(y[k]), __uint_as_float(x[k])));
+        }
+        if (last) {
+#pragma unroll
+          for (int k = 0; k < 32; k += 4)
+            *reinterpret_cast<float4*>(drow + c + k) = make_float4(__uint_as_float(x[k]), __uint_as_float(x[k + 1]),
+                                                                   __uint_as_float(x[k + 2]), __uint_as_float(x[k + 3]));
+        } else {
+          tmem_st32(t_sum + lanes + c, x);
+        }
+      }
+      if (!last) tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pfree[b]);
+    }
+    if (!ok && lane == 0) atomicOr(p.err, kErrTmaTimeout);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*taddr_s), "r"(kTmemCols) : "memory");
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t_sum), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Sum of the split-K groups' partial results, in group order (each group already folded its
+// chunks in order): out[i] = ((part[0][i] + part[1][i]) + ...).
+__global__ void tc_reduce_kernel(const float4* part, float4* out, size_t n4, size_t group4, int groups) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n4;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    float4 a = part[i];
+    for (int gi = 1; gi < groups; ++gi) {
+      const float4 b = part[gi * group4 + i];
+      a = make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+    }
+    out[i] = a;
   }
 }
 
 // ---- forward: phase rotation, A-point DFT over the sub-block phase, twiddle ----------------
-// One CTA per (station, channel), thread n2; writes the GEMM rows ((s * 2 + c) * A + j1) of
-// 512 interleaved complex values W[j1][n2].
+// One CTA per (station, channel), thread n2; writes W[j1][n2] as GEMM row ((s * 2 + c) * A + j1),
+// complex column n2, into the BF16 planes of the forward GEMM's A image.
+struct SplitImage {
+  __nv_bfloat16* plane[3];
+  int planes;
+};
+
 template <int N_>
-__global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_constant__ EventDesc ev, float2* w) {
+__global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_constant__ EventDesc ev,
+                                                              const __grid_constant__ SplitImage img) {
   constexpr int N = N_, A = N / kSub;
   const int sc = blockIdx.x, n2 = threadIdx.x;
   const float* x = ev.traces + static_cast<size_t>(sc) * N;
@@ -257,16 +317,17 @@ __global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_const
 #pragma unroll
   for (int j1 = 0; j1 < A; ++j1) {
     const float2 t = j1 == 0 ? y[0] : cmul(y[j1], __ldg(ev.wn + j1 * n2));   // exp(-2 pi i j1 n2 / N)
-    w[(static_cast<size_t>(sc) * A + j1) * kSub + n2] = t;
+    put_split(img.plane, img.planes, image_offset(sc * A + j1, 2 * n2, kFwdK), t);
   }
 }
 
 // ---- per pair: VEL interpolation and 2x2 solve (as the FP32 path) -> inverse GEMM rows ----
 // One CTA per pair of the chunk [pair0, pair0 + gridDim.x); the forward GEMM output holds
-// X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2.
+// X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2. Writes Zf as GEMM row
+// ((lp * 2 + pol) * A + j1), complex column j2, into the inverse GEMM's A image.
 template <int N_>
 __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ EventDesc ev, const float2* xf,
-                                                       float2* z, long long pair0) {
+                                                       const __grid_constant__ SplitImage img, long long pair0) {
   constexpr int N = N_, M = N / 4, A = N / kSub;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* hn = reinterpret_cast<float2*>(smem_raw);   // [n_f][8]: 4 values, 4 slopes
@@ -298,8 +359,6 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
   constexpr float kScale = 2.0f / static_cast<float>(N);
   const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
   const float2* x1 = x0 + A * kBandPhase;
-  float2* zt = z + static_cast<size_t>(lp * 2) * A * kBandPhase;
-  float2* zp = zt + A * kBandPhase;
   for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
     const int j1 = i / kBandPhase, j2 = i % kBandPhase;
     const int j = j1 + A * j2;
@@ -328,8 +387,8 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
         sing = true;
       }
     }
-    zt[i] = et;
-    zp[i] = ep;
+    put_split(img.plane, img.planes, image_offset((lp * 2) * A + j1, 2 * j2, kInvK), et);
+    put_split(img.plane, img.planes, image_offset((lp * 2 + 1) * A + j1, 2 * j2, kInvK), ep);
   }
   const bool any = __syncthreads_or(sing);
   if (tid == 0) ev.status[pair] = di.st | (any ? kStSingular : 0u);
