@@ -64,6 +64,7 @@ typedef enum ar_status {
 #define AR_STATUS_SINGULAR 1u    /* at least one in-band bin was near-singular (E set to 0) */
 #define AR_STATUS_ZEN_CLAMP 2u   /* the zenith lay outside the table and was clamped        */
 #define AR_STATUS_BAD_DIR 4u     /* the direction was not finite: every output of the pair is 0 */
+#define AR_STATUS_BAD_PATTERN 8u /* station_pattern named no loaded pattern: every output is 0 */
 
 typedef struct ar_ctx ar_ctx;
 
@@ -87,13 +88,20 @@ typedef struct ar_event {
   int32_t n_stations;          /* S >= 1                                                   */
   int32_t n_samples;           /* N: 1024, 2048 or 4096                                    */
   int32_t n_dirs;              /* D >= 1                                                   */
-  int32_t pattern_id;          /* from ar_load_pattern; every station uses this pattern    */
+  int32_t pattern_id;          /* from ar_load_pattern; every station uses this pattern
+                                  unless station_pattern is given (it must be loaded still) */
   double fs_hz;                /* sample rate                                              */
   double refractive_index;     /* n_refr of the plane-wave model; 0 means 1.0              */
   const float* traces;         /* [S][2][N] float32 voltages; 16-byte aligned              */
   const double* pos_m;         /* [S][3] station positions, metres                         */
   const double* t_start_ns;    /* [S] time of sample 0 of each station's trace, ns         */
   const double* dirs_rad;      /* [D][2] (zenith, azimuth), radians                        */
+  const int32_t* station_pattern; /* [S] pattern id of each station's antenna (Sec. 3: every
+                                  AERA antenna type's pattern resident at once), or NULL.
+                                  Patterns may differ in grid. An id that was never loaded
+                                  gives AR_STATUS_BAD_PATTERN and zero outputs for that
+                                  station's pairs. Stations grouped by pattern are fastest
+                                  (the interpolation is redone where the pattern changes). */
 } ar_event;
 
 /* Outputs, owned by the caller (DEVICE memory for ar_unfold, HOST memory for
@@ -316,7 +324,7 @@ ar_status ar_server_destroy(ar_server* server);
  * present on every GPU that loads it until the process exits.
  *  - Limits: n_stations x n_samples <= 983,040 (240 stations of 4096 samples, 480 of 2048,
  *    960 of 1024) and n_dirs <= 4096; larger events return AR_ERR_INVALID_ARG and a
- *    message naming the limit.
+ *    message naming the limit. One pattern per call: ev->station_pattern must be NULL.
  *  - Set-up: the first call on a device (with that device current) looks up the array's
  *    device address and sets kernel attributes; make that first call before any stream
  *    capture.

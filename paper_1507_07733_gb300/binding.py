@@ -61,7 +61,8 @@ class ar_event(ctypes.Structure):
     _fields_ = [("n_stations", ctypes.c_int32), ("n_samples", ctypes.c_int32), ("n_dirs", ctypes.c_int32),
                 ("pattern_id", ctypes.c_int32), ("fs_hz", ctypes.c_double),
                 ("refractive_index", ctypes.c_double), ("traces", ctypes.c_void_p),
-                ("pos_m", ctypes.c_void_p), ("t_start_ns", ctypes.c_void_p), ("dirs_rad", ctypes.c_void_p)]
+                ("pos_m", ctypes.c_void_p), ("t_start_ns", ctypes.c_void_p), ("dirs_rad", ctypes.c_void_p),
+                ("station_pattern", ctypes.c_void_p)]
 
 
 class ar_batch_limits(ctypes.Structure):
@@ -294,12 +295,16 @@ def _ptr(t):
 
 
 def make_event(pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
-               refractive_index: float = 1.0) -> ar_event:
-    """Build an ``ar_event`` from tensors (device or host, matching the call used)."""
+               refractive_index: float = 1.0, station_pattern=None) -> ar_event:
+    """Build an ``ar_event`` from tensors (device or host, matching the call used);
+    ``station_pattern`` is an optional int32 tensor of pattern ids, one per station."""
     S, two, N = traces.shape
     assert two == 2
+    if station_pattern is not None:
+        assert station_pattern.dtype.itemsize == 4 and station_pattern.numel() == S
     return ar_event(S, N, dirs_rad.shape[0], pattern_id, fs_hz, refractive_index,
-                    _ptr(traces), _ptr(pos_m), _ptr(t_start_ns), _ptr(dirs_rad))
+                    _ptr(traces), _ptr(pos_m), _ptr(t_start_ns), _ptr(dirs_rad),
+                    _ptr(station_pattern) if station_pattern is not None else None)
 
 
 def alloc_outputs(n_dirs: int, n_stations: int, n_samples: int, device="cuda", traces: bool = True,
@@ -355,14 +360,14 @@ class Context:
 
     def unfold(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
                refractive_index: float = 1.0, out: dict | None = None, traces_out: bool = True,
-               stream=None, sync: bool = False) -> dict:
+               stream=None, sync: bool = False, station_pattern=None) -> dict:
         """Unfold an event held in device tensors; returns the output tensors (async unless sync)."""
         import torch
         S, _, N = traces.shape
         D = dirs_rad.shape[0]
         if out is None:
             out, _ = alloc_outputs(D, S, N, device=traces.device, traces=traces_out)
-        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index, station_pattern)
         st = stream if stream is not None else torch.cuda.current_stream(traces.device)
         ar_unfold(self.h, ev, outputs_struct(out), st.cuda_stream)
         if sync:
@@ -371,14 +376,14 @@ class Context:
 
     def unfold_tc(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, split_terms: int = 3,
                   fs_hz: float = 200e6, refractive_index: float = 1.0, out: dict | None = None,
-                  traces_out: bool = True, stream=None, sync: bool = False) -> dict:
+                  traces_out: bool = True, stream=None, sync: bool = False, station_pattern=None) -> dict:
         """ar_unfold_tc: the tensor-core DFT variant (split-BF16 x3 or x6) on device tensors."""
         import torch
         S, _, N = traces.shape
         D = dirs_rad.shape[0]
         if out is None:
             out, _ = alloc_outputs(D, S, N, device=traces.device, traces=traces_out)
-        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index, station_pattern)
         st = stream if stream is not None else torch.cuda.current_stream(traces.device)
         ar_unfold_tc(self.h, ev, outputs_struct(out), split_terms, st.cuda_stream)
         if sync:
@@ -419,14 +424,14 @@ class Context:
 
     def unfold_host(self, pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
                     refractive_index: float = 1.0, out: dict | None = None, traces_out: bool = True,
-                    stream=None) -> dict:
+                    stream=None, station_pattern=None) -> dict:
         """ar_unfold_host: inputs and outputs are host (CPU) tensors; returns when done."""
         import torch
         S, _, N = traces.shape
         D = dirs_rad.shape[0]
         if out is None:
             out, _ = alloc_outputs(D, S, N, device="cpu", traces=traces_out)
-        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index)
+        ev = make_event(pattern_id, traces, pos_m, t_start_ns, dirs_rad, fs_hz, refractive_index, station_pattern)
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         ar_unfold_host(self.h, ev, outputs_struct(out), st.cuda_stream)
         return out

@@ -66,6 +66,11 @@ struct ar_ctx {
   std::map<std::pair<int, int>, LenTables> len_tables;                 // (N, k_lo)
   std::map<std::tuple<int, double, int>, int2*> bin_tables;            // (N, fs, pattern)
   std::map<std::pair<int, int>, KernelCfg> unfold_cfg;                 // (N, n_f)
+  // per (N, fs): every loaded pattern as the kernels see it (for per-station pattern ids),
+  // with the number of patterns it was built for; replaced tables stay allocated until destroy
+  std::map<std::pair<int, double>, std::pair<PatternRef*, int>> pattern_refs;
+  std::vector<PatternRef*> retired_refs;
+  int max_nf = 0;                 // the most frequency nodes of any loaded pattern
   float4* spec = nullptr;
   size_t spec_bytes = 0;
   unsigned* dir_done = nullptr;   // [max directions] completion counters of the fused residual
@@ -216,6 +221,56 @@ ar_status get_bin_table(ar_ctx* ctx, int n, double fs, int pid, int k_lo, int2**
   return AR_OK;
 }
 
+// Every loaded pattern at (N, fs) as the kernels see it, indexed by pattern id.
+ar_status get_pattern_refs(ar_ctx* ctx, int n, double fs, int k_lo, const PatternRef** out, int* count) {
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  const int np = static_cast<int>(ctx->patterns.size());
+  auto key = std::make_pair(n, fs);
+  auto it = ctx->pattern_refs.find(key);
+  if (it == ctx->pattern_refs.end() || it->second.second != np) {
+    std::vector<PatternRef> refs(np);
+    for (int i = 0; i < np; ++i) {
+      const ar_pattern_desc& pd = ctx->patterns[i].desc;
+      int2* binf = nullptr;
+      ar_status st = get_bin_table(ctx, n, fs, i, k_lo, &binf);
+      if (st != AR_OK) return st;
+      refs[i] = PatternRef{ctx->patterns[i].table, binf, pd.zen0_rad, pd.dzen_rad, pd.az0_rad, pd.daz_rad,
+                           pd.n_zen, pd.n_az, pd.n_freq, 0};
+    }
+    PatternRef* d = nullptr;
+    AR_CUDA(ctx, cudaMalloc(&d, refs.size() * sizeof(PatternRef)));
+    AR_CUDA(ctx, cudaMemcpy(d, refs.data(), refs.size() * sizeof(PatternRef), cudaMemcpyHostToDevice));
+    if (it != ctx->pattern_refs.end()) {
+      ctx->retired_refs.push_back(it->second.first);   // a launch in flight may still read it
+      it->second = {d, np};
+    } else {
+      it = ctx->pattern_refs.emplace(key, std::make_pair(d, np)).first;
+    }
+  }
+  *out = it->second.first;
+  *count = it->second.second;
+  return AR_OK;
+}
+
+// frequency nodes the unfold kernel lays its shared memory out for
+int layout_nf(const ar_ctx* ctx, const ar_event* ev) {
+  return ev->station_pattern ? ctx->max_nf : ctx->patterns[ev->pattern_id].desc.n_freq;
+}
+
+// per-station patterns: point the descriptor at the pattern table and the caller's ids
+ar_status attach_patterns(ar_ctx* ctx, const ar_event* ev, int k_lo, EventDesc* d) {
+  if (!ev->station_pattern) return AR_OK;
+  const PatternRef* refs = nullptr;
+  int count = 0;
+  ar_status st = get_pattern_refs(ctx, ev->n_samples, ev->fs_hz, k_lo, &refs, &count);
+  if (st != AR_OK) return st;
+  d->pats = refs;
+  d->st_pat = ev->station_pattern;
+  d->n_pats = count;
+  d->n_f_layout = ctx->max_nf;
+  return AR_OK;
+}
+
 ar_status ensure_dirs(ar_ctx* ctx, size_t n_dir) {
   if (n_dir <= ctx->dir_cap) return AR_OK;
   if (ctx->dir_done) {
@@ -252,8 +307,10 @@ ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
   if (it == ctx->unfold_cfg.end()) {
     KernelCfg kc;
     kc.smem = UnfoldSmem<N_>::total(n_f);
+    // the attribute belongs to the kernel, not to this configuration: set it to the largest
+    // layout any pattern can need, so that no later set-up lowers it below a cached launch
     AR_CUDA(ctx, cudaFuncSetAttribute(unfold_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(kc.smem)));
+                                      static_cast<int>(UnfoldSmem<N_>::total(kMaxFreqNodes))));
     int per_sm = 0;
     AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, Layout<N_>::T,
                                                                kc.smem));
@@ -290,12 +347,12 @@ ar_status validate_shape(ar_ctx* ctx, int n, double fs, int pid, int* k_lo) {
   return AR_OK;
 }
 
-ar_status resolve(ar_ctx* ctx, int n, double fs, int pid, int max_st, Resolved* rs) {
+ar_status resolve(ar_ctx* ctx, int n, double fs, int pid, int max_st, Resolved* rs, int n_f_layout = 0) {
   ar_status st = validate_shape(ctx, n, fs, pid, &rs->k_lo);
   if (st != AR_OK) return st;
   if ((st = get_len_tables(ctx, n, rs->k_lo, &rs->lt)) != AR_OK) return st;
   if ((st = get_bin_table(ctx, n, fs, pid, rs->k_lo, &rs->binf)) != AR_OK) return st;
-  const int n_f = ctx->patterns[pid].desc.n_freq;
+  const int n_f = n_f_layout > 0 ? n_f_layout : ctx->patterns[pid].desc.n_freq;
   st = n == 1024 ? unfold_cfg<1024>(ctx, n_f, &rs->kc)
        : n == 2048 ? unfold_cfg<2048>(ctx, n_f, &rs->kc)
                    : unfold_cfg<4096>(ctx, n_f, &rs->kc);
@@ -368,6 +425,7 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.n_zen = pd.n_zen;
   d.n_az = pd.n_az;
   d.n_f = pd.n_freq;
+  d.n_f_layout = pd.n_freq;
   d.n_st = ev->n_stations;
   d.n_dir = ev->n_dirs;
   d.k_lo = k_lo;
@@ -376,25 +434,24 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
 
 // one event: the station kernel (one CTA per station), then the persistent unfold kernel
 template <int N_>
-cudaError_t launch_path(const PathBuffers& b, const ar_pattern_desc& pd, const float2* table, const ar_event* ev,
-                        const ar_outputs* out, int k_lo, int grid_cap, cudaStream_t stream,
+cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cudaStream_t stream,
                         cudaEvent_t* evs /* 3 events or null */) {
   using L = Layout<N_>;
   PathParams pp{};
   pp.batch = nullptr;
-  pp.err = b.err;
+  pp.err = err;
   pp.wait_prior = 1;
-  pp.ev0 = make_desc(b, pd, table, ev, out, k_lo);
+  pp.ev0 = desc;
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, ev->n_stations, L::T, SpectrumSmem<N_>::TOTAL, stream, pp)) !=
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, desc.n_st, L::T, SpectrumSmem<N_>::TOTAL, stream, pp)) !=
       cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
-  const long long pairs = static_cast<long long>(ev->n_stations) * ev->n_dirs;
+  const long long pairs = static_cast<long long>(desc.n_st) * desc.n_dir;
   const long long grid = std::min<long long>(grid_cap, pairs);
-  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T, UnfoldSmem<N_>::total(pd.n_freq), stream,
-                      pp)) != cudaSuccess)
+  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T, UnfoldSmem<N_>::total(pp.ev0.n_f_layout),
+                      stream, pp)) != cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[2], stream)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -405,8 +462,10 @@ ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, con
                      cudaStream_t stream) {
   const PatternDev& pat = ctx->patterns[ev->pattern_id];
   PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
-  cudaError_t e = launch_path<N_>(b, pat.desc, pat.table, ev, out, rs.k_lo, rs.kc->grid, stream,
-                                  ctx->profiling ? ctx->ev : nullptr);
+  EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
+  ar_status st = attach_patterns(ctx, ev, rs.k_lo, &desc);
+  if (st != AR_OK) return st;
+  cudaError_t e = launch_path<N_>(ctx->d_err, desc, rs.kc->grid, stream, ctx->profiling ? ctx->ev : nullptr);
   if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
   if (ctx->profiling) {
     ctx->timed = true;
@@ -497,6 +556,8 @@ ar_status ar_destroy(ar_ctx* ctx) {
     cudaFree(kv.second.wn);
   }
   for (auto& kv : ctx->bin_tables) cudaFree(kv.second);
+  for (auto& kv : ctx->pattern_refs) cudaFree(kv.second.first);
+  for (auto* p : ctx->retired_refs) cudaFree(p);
   for (auto& s : ctx->stage) cudaFree(s.first);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -542,6 +603,7 @@ ar_status ar_load_pattern(ar_ctx* ctx, const ar_pattern_desc* d, const float* ho
     return fail(ctx, AR_ERR_CUDA, "pattern upload failed: %s", cudaGetErrorString(e));
   }
   ctx->patterns.push_back(p);
+  ctx->max_nf = std::max(ctx->max_nf, d->n_freq);
   *pattern_id = static_cast<int32_t>(ctx->patterns.size() - 1);
   return AR_OK;
 }
@@ -560,7 +622,9 @@ ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void
   if (st != AR_OK) return st;
   AR_CUDA(ctx, cudaSetDevice(ctx->device));
   Resolved rs;
-  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs, layout_nf(ctx, ev))) !=
+      AR_OK)
+    return st;
   if ((st = resolve_dirs(ctx, ev->n_dirs)) != AR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (ev->n_samples) {
@@ -590,6 +654,7 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   pp.skip = &st->converged;
   pp.wait_prior = 1;
   pp.ev0 = make_desc(b, pat.desc, pat.table, &e1, &out->last, rs.k_lo);
+  if (attach_patterns(ctx, &e1, rs.k_lo, &pp.ev0) != AR_OK) return cudaErrorMemoryAllocation;
   const int S = ev->n_stations;
   const double dt_ns = 1e9 / ev->fs_hz;
   const double n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
@@ -606,7 +671,7 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
   plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
   for (int it = 1; it <= max_iter; ++it) {
-    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T, UnfoldSmem<N_>::total(pat.desc.n_freq),
+    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T, UnfoldSmem<N_>::total(pp.ev0.n_f_layout),
                         stream, pp)) != cudaSuccess)
       return e;
     fp.times = out->last.peak_time_ns;
@@ -638,8 +703,14 @@ ar_status ar_reconstruct(ar_ctx* ctx, const ar_event* ev, int32_t max_iter, doub
   if (ev->n_stations < 3) return fail(ctx, AR_ERR_INVALID_ARG, "a direction fit needs at least 3 stations");
   AR_CUDA(ctx, cudaSetDevice(ctx->device));
   Resolved rs;
-  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs, layout_nf(ctx, ev))) !=
+      AR_OK)
+    return st;
   if ((st = resolve_dirs(ctx, 1)) != AR_OK) return st;
+  {
+    EventDesc probe{};
+    if ((st = attach_patterns(ctx, ev, rs.k_lo, &probe)) != AR_OK) return st;   // builds the pattern table
+  }
   const size_t S = ev->n_stations;
   const size_t need = 256 + S * (4 + 8 + 4) + 3 * 256;
   if (need > ctx->recon_bytes) {
@@ -685,14 +756,15 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   if (N != 1024 && N != 2048 && N != 4096)
     return fail(ctx, AR_ERR_UNSUPPORTED_N, "n_samples=%zu: supported lengths are 1024, 2048, 4096", N);
   // staging slots: 0 traces, 1 pos, 2 t_start, 3 dirs, 4 efield, 5 envelope, 6 peak_idx,
-  // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status
-  const size_t sizes[13] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
+  // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status, 13 station patterns
+  const size_t sizes[14] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
                             D * 2 * sizeof(double), out->efield ? D * S * 2 * N * sizeof(float) : 0,
                             out->envelope ? D * S * N * sizeof(float) : 0, D * S * sizeof(int32_t),
                             D * S * sizeof(float), D * S * sizeof(double), D * S * sizeof(double),
-                            D * sizeof(double), D * sizeof(double), D * S * sizeof(uint32_t)};
-  if (ctx->stage.size() < 13) ctx->stage.resize(13, {nullptr, 0});
-  for (int i = 0; i < 13; ++i) {
+                            D * sizeof(double), D * sizeof(double), D * S * sizeof(uint32_t),
+                            ev->station_pattern ? S * sizeof(int32_t) : 0};
+  if (ctx->stage.size() < 14) ctx->stage.resize(14, {nullptr, 0});
+  for (int i = 0; i < 14; ++i) {
     if (sizes[i] > ctx->stage[i].second) {
       AR_CUDA(ctx, cudaDeviceSynchronize());
       cudaFree(ctx->stage[i].first);
@@ -707,7 +779,10 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   AR_CUDA(ctx, cudaMemcpyAsync(dev(1), ev->pos_m, sizes[1], cudaMemcpyHostToDevice, s));
   AR_CUDA(ctx, cudaMemcpyAsync(dev(2), ev->t_start_ns, sizes[2], cudaMemcpyHostToDevice, s));
   AR_CUDA(ctx, cudaMemcpyAsync(dev(3), ev->dirs_rad, sizes[3], cudaMemcpyHostToDevice, s));
+  if (ev->station_pattern)
+    AR_CUDA(ctx, cudaMemcpyAsync(dev(13), ev->station_pattern, sizes[13], cudaMemcpyHostToDevice, s));
   ar_event de = *ev;
+  de.station_pattern = ev->station_pattern ? static_cast<const int32_t*>(dev(13)) : nullptr;
   de.traces = static_cast<const float*>(dev(0));
   de.pos_m = static_cast<const double*>(dev(1));
   de.t_start_ns = static_cast<const double*>(dev(2));
@@ -907,7 +982,7 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   tc::tc_forward_pre_kernel<N_><<<2 * S, tc::kSub, 0, stream>>>(ev, fimg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_gemm(ctx, w.fa, rows_f, 0, terms, w.xf, w.part, stream)) != cudaSuccess) return e;
-  const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f);
+  const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
     tc::tc_solve_kernel<N_><<<np, 256, solve_smem, stream>>>(ev, reinterpret_cast<const float2*>(w.xf), zimg, p0);
@@ -944,7 +1019,9 @@ ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, i
   }
   AR_CUDA(ctx, cudaSetDevice(ctx->device));
   Resolved rs;
-  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs)) != AR_OK) return st;
+  if ((st = resolve(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, ev->n_stations, &rs, layout_nf(ctx, ev))) !=
+      AR_OK)
+    return st;
   if ((st = resolve_dirs(ctx, ev->n_dirs)) != AR_OK) return st;
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -966,7 +1043,8 @@ ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, i
   }
   const PatternDev& pat = ctx->patterns[ev->pattern_id];
   PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
-  const EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
+  EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
+  if ((st = attach_patterns(ctx, ev, rs.k_lo, &desc)) != AR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int terms = split_terms;
   cudaError_t e = ev->n_samples == 1024   ? launch_tc<1024>(ctx, desc, terms, rows_f, chunk, s)
@@ -1095,9 +1173,9 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
     Resolved rs;
     if ((st = validate_shape(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, &rs.k_lo)) != AR_OK)
       return fail(ctx, st, "event %d: %s", i, ctx->last_error.c_str());
-    if (ctx->patterns[ev->pattern_id].desc.n_freq > b->lim.max_n_freq)
-      return fail(ctx, AR_ERR_INVALID_ARG, "event %d: pattern has %d frequency nodes, plan allows %d", i,
-                  ctx->patterns[ev->pattern_id].desc.n_freq, b->lim.max_n_freq);
+    if (layout_nf(ctx, ev) > b->lim.max_n_freq)
+      return fail(ctx, AR_ERR_INVALID_ARG, "event %d: its patterns have %d frequency nodes, plan allows %d", i,
+                  layout_nf(ctx, ev), b->lim.max_n_freq);
     if ((st = get_len_tables(ctx, ev->n_samples, rs.k_lo, &rs.lt)) != AR_OK) return st;
     if ((st = get_bin_table(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, rs.k_lo, &rs.binf)) != AR_OK) return st;
     stations += ev->n_stations;
@@ -1111,6 +1189,8 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
                    b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
     const PatternDev& pat = ctx->patterns[ev->pattern_id];
     EventDesc d = make_desc(pb, pat.desc, pat.table, ev, &outs[i], rs.k_lo);
+    if ((st = attach_patterns(ctx, ev, rs.k_lo, &d)) != AR_OK) return st;
+    d.n_f_layout = b->lim.max_n_freq;   // the plan's shared-memory layout
     d.pair_begin = hdr[c]->total_pairs;
     d.station_begin = hdr[c]->total_stations;
     dsc[c][hdr[c]->n_events++] = d;
@@ -1166,7 +1246,11 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
     const void* sfn = c == 0 ? reinterpret_cast<const void*>(station_spectrum_kernel<1024>)
                       : c == 1 ? reinterpret_cast<const void*>(station_spectrum_kernel<2048>)
                                : reinterpret_cast<const void*>(station_spectrum_kernel<4096>);
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) != cudaSuccess ||
+    const size_t smem_max = c == 0 ? UnfoldSmem<1024>::total(kMaxFreqNodes)
+                            : c == 1 ? UnfoldSmem<2048>::total(kMaxFreqNodes)
+                                     : UnfoldSmem<4096>::total(kMaxFreqNodes);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max))) !=
+            cudaSuccess ||
         (e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp_smem))) != cudaSuccess ||
         (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas_per_sm[c], fn, threads, smem)) != cudaSuccess)
       return cleanup(fail(ctx, AR_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e)));
@@ -1368,6 +1452,7 @@ size_t req_state_bytes(const ar_event& ev, const ar_outputs& out) {
   const size_t S = ev.n_stations, D = ev.n_dirs, N = ev.n_samples;
   auto r = [](size_t x) { return (x + 255) / 256 * 256; };
   size_t b = r(S * 2 * N * 4) + r(S * 24) + r(S * 8) + r(D * 16);
+  if (ev.station_pattern) b += r(S * 4);
   if (out.efield) b += r(D * S * 2 * N * 4);
   if (out.envelope) b += r(D * S * N * 4);
   b += r(D * S * 4) * 2 + r(D * S * 8) * 2 + r(D * 8) * 2 + r(D * S * 4);
@@ -1410,6 +1495,7 @@ void place_request(ar_server* sv, Request& r) {
   r.dev_ev.pos_m = reinterpret_cast<const double*>(take(S * 24));
   r.dev_ev.t_start_ns = reinterpret_cast<const double*>(take(S * 8));
   r.dev_ev.dirs_rad = reinterpret_cast<const double*>(take(D * 16));
+  if (r.ev.station_pattern) r.dev_ev.station_pattern = reinterpret_cast<const int32_t*>(take(S * 4));
   r.dev_out = ar_outputs{};
   if (r.out.efield) r.dev_out.efield = reinterpret_cast<float*>(take(D * S * 2 * N * 4));
   if (r.out.envelope) r.dev_out.envelope = reinterpret_cast<float*>(take(D * S * N * 4));
@@ -1434,6 +1520,9 @@ cudaError_t copy_in(ar_server* sv, const Request& r) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(const_cast<double*>(r.dev_ev.dirs_rad), r.ev.dirs_rad, D * 16, cudaMemcpyHostToDevice,
                         sv->s_h2d);
+  if (e == cudaSuccess && r.ev.station_pattern)
+    e = cudaMemcpyAsync(const_cast<int32_t*>(r.dev_ev.station_pattern), r.ev.station_pattern, S * 4,
+                        cudaMemcpyHostToDevice, sv->s_h2d);
   return e;
 }
 
@@ -1608,6 +1697,9 @@ ar_status ar_submit(ar_server* sv, const ar_event* ev, const ar_outputs* out, ui
   if (st != AR_OK) return st;
   int k_lo = 0;
   if ((st = validate_shape(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, &k_lo)) != AR_OK) return st;
+  if (layout_nf(ctx, ev) > sv->cfg.max_n_freq)
+    return fail(ctx, AR_ERR_INVALID_ARG, "the event's patterns have %d frequency nodes, the server allows %d",
+                layout_nf(ctx, ev), sv->cfg.max_n_freq);
   if (ev->n_stations > sv->cfg.max_stations_per_event || ev->n_dirs > 256)
     return fail(ctx, AR_ERR_BUDGET, "event larger than the server's per-event limits (%d stations, 256 directions)",
                 sv->cfg.max_stations_per_event);
@@ -1842,8 +1934,8 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
   AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T,
                                                            UnfoldSmem<N_>::total(pd->n_freq)));
   if (per_sm < 1) return noalloc_fail(AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM", N_);
-  AR_NA_CUDA(launch_path<N_>(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo, per_sm * nd.num_sms,
-                             stream, nullptr));
+  const EventDesc desc = make_desc(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo);
+  AR_NA_CUDA(launch_path<N_>(b.err, desc, per_sm * nd.num_sms, stream, nullptr));
   return AR_OK;
 }
 
@@ -1861,6 +1953,8 @@ ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const
       std::fabs(pd->n_az * pd->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
     return noalloc_fail(AR_ERR_INVALID_ARG, "bad pattern descriptor");
   if (!ev || !out) return noalloc_fail(AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+  if (ev->station_pattern)
+    return noalloc_fail(AR_ERR_INVALID_ARG, "per-station patterns need a context (ar_unfold); station_pattern must be NULL");
   if (ev->n_stations < 1 || ev->n_dirs < 1 || ev->n_dirs > kNoAllocMaxDirs)
     return noalloc_fail(AR_ERR_INVALID_ARG, "n_stations must be >= 1 and n_dirs in [1, %d]", kNoAllocMaxDirs);
   if (ev->n_samples != 1024 && ev->n_samples != 2048 && ev->n_samples != 4096)

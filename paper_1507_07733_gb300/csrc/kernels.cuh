@@ -32,6 +32,7 @@ namespace aerafold {
 constexpr unsigned kStSingular = 1u;
 constexpr unsigned kStZenClamp = 2u;
 constexpr unsigned kStBadDir = 4u;
+constexpr unsigned kStBadPattern = 8u;
 
 constexpr unsigned kErrTmaTimeout = 1u;     // a bounded mbarrier wait ran out
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
@@ -149,6 +150,15 @@ __device__ __forceinline__ void pdl_wait_prior() {
 
 // ---- events as the kernels see them ------------------------------------------------------
 
+// One antenna pattern as the kernels see it: its table, its frequency cell per band bin at
+// the event's (N, fs), and its axes.
+struct PatternRef {
+  const float2* table;     // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
+  const int2* binf;        // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
+  double zen0, dzen, az0, daz;
+  int n_zen, n_az, n_f, pad;
+};
+
 // One event. A plain call passes it inline in the kernel parameters; a batch launch reads
 // an array of them, behind a header, from device memory (so a captured graph can be
 // replayed with new events after a copy into that memory).
@@ -173,11 +183,14 @@ struct EventDesc {
   const float2* t1;        // [4][Q][P] pass-1 output twiddles
   const float2* twf;       // [Q][P] forward pass twiddles exp(-2 pi i p q / M) at [q][p]
   const float2* wn;        // [N] exp(-2 pi i t / N)
+  const PatternRef* pats;  // with st_pat: the loaded patterns at this (N, fs), by pattern id
+  const int* st_pat;       // [S] pattern id per station, or null: every station uses the fields here
   double zen0, dzen, az0, daz, dt_ns, n_over_c;
   long long pair_begin;    // first pair of the event in the launch's flattened pair space
   int station_begin;       // first station of the event in the launch's flattened station space
   int n_zen, n_az, n_f, n_st, n_dir, k_lo;
-  int pad;
+  int n_pats;
+  int n_f_layout;          // frequency nodes the unfold kernel's shared memory is laid out for (>= any pattern's)
 };
 
 struct BatchHeader {       // in device memory, followed by EventDesc[n_events] (16-byte aligned)
@@ -208,6 +221,29 @@ __device__ __forceinline__ int find_event(int n, long long x, F begin_of) {
     if (begin_of(mid) <= x) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Pattern of station s: an index into ev.pats, -1 for the event's own pattern (no per-station
+// ids), or -2 for an id outside the loaded patterns (the pair's outputs are then zero).
+__device__ __forceinline__ int station_pattern(const EventDesc& ev, int s) {
+  if (!ev.st_pat) return -1;
+  const int p = ev.st_pat[s];
+  return (p >= 0 && p < ev.n_pats) ? p : -2;
+}
+__device__ __forceinline__ PatternRef pattern_ref(const EventDesc& ev, int p) {
+  if (p >= 0) return ev.pats[p];
+  PatternRef r;
+  r.table = ev.table;
+  r.binf = ev.binf;
+  r.zen0 = ev.zen0;
+  r.dzen = ev.dzen;
+  r.az0 = ev.az0;
+  r.daz = ev.daz;
+  r.n_zen = ev.n_zen;
+  r.n_az = ev.n_az;
+  r.n_f = ev.n_f;
+  r.pad = 0;
+  return r;
 }
 
 // copy an event descriptor word by word (whole CTA)
@@ -320,14 +356,14 @@ struct DirInfo {
   int slab0, slab1, slab2, slab3;   // node offsets (units of n_f * 4 float2) of the 4 corners
   float w[4];                       // bilinear weights of the corners
   unsigned st;
-  int pad;
+  int pat;                          // the station pattern the cell belongs to (station_pattern)
 };
 
 // Direction -> pattern cell (FP64, no fused multiply-adds) -> FP32 bilinear weights.
-__device__ __forceinline__ DirInfo direction_cell(const EventDesc& p, double zen, double az) {
+__device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double zen, double az) {
   DirInfo di;
   di.st = 0;
-  di.pad = 0;
+  di.pat = -1;
   if (!isfinite(zen) || !isfinite(az)) {
     di.st = kStBadDir;
     di.slab0 = di.slab1 = di.slab2 = di.slab3 = 0;
@@ -461,21 +497,40 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   }
 }
 
+// Direction cell of pair (d, s) in the station's pattern (pattern index p from station_pattern).
+__device__ __forceinline__ DirInfo pair_cell(const EventDesc& ev, int d, int p, PatternRef* pr_out) {
+  const PatternRef pr = pattern_ref(ev, p);
+  DirInfo di = direction_cell(pr, ev.dirs[2 * d], ev.dirs[2 * d + 1]);
+  if (p == -2) {   // not a loaded pattern: no interpolation, every output of the pair is zero
+    di.st = kStBadPattern;
+    di.slab0 = di.slab1 = di.slab2 = di.slab3 = 0;
+    di.w[0] = di.w[1] = di.w[2] = di.w[3] = 0.f;
+  }
+  di.pat = p;
+  if (pr_out) *pr_out = pr;
+  return di;
+}
+
 // Issue the bulk copies of one pair's inputs: the station's band spectrum and, for a new
-// direction, its four corner slabs (thread 0 only).
-__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, bool new_dir, DirInfo* sdir,
-                                                  float2* slab, float4* sspec, uint64_t* bar, int m) {
+// (direction, pattern), the four corner slabs of the station's pattern (thread 0 only).
+__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, int p, bool new_key,
+                                                  DirInfo* sdir, float2* slab, float4* sspec, uint64_t* bar, int m) {
   const unsigned spec_bytes = static_cast<unsigned>(sizeof(float4)) * m;
-  const unsigned slab_bytes = static_cast<unsigned>(ev.n_f) * 4u * sizeof(float2);
-  const size_t node = static_cast<size_t>(ev.n_f) * 4;
-  if (new_dir) {
-    const DirInfo di = direction_cell(ev, ev.dirs[2 * d], ev.dirs[2 * d + 1]);
+  if (new_key) {
+    PatternRef pr;
+    const DirInfo di = pair_cell(ev, d, p, &pr);
     *sdir = di;
-    mbar_arrive_expect_tx(bar, spec_bytes + 4 * slab_bytes);
-    tma_bulk_g2s(slab + 0 * node, ev.table + di.slab0 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 1 * node, ev.table + di.slab1 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 2 * node, ev.table + di.slab2 * node, slab_bytes, bar);
-    tma_bulk_g2s(slab + 3 * node, ev.table + di.slab3 * node, slab_bytes, bar);
+    if (p == -2) {
+      mbar_arrive_expect_tx(bar, spec_bytes);
+    } else {
+      const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
+      const size_t node = static_cast<size_t>(pr.n_f) * 4;
+      mbar_arrive_expect_tx(bar, spec_bytes + 4 * slab_bytes);
+      tma_bulk_g2s(slab + 0 * node, pr.table + di.slab0 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 1 * node, pr.table + di.slab1 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 2 * node, pr.table + di.slab2 * node, slab_bytes, bar);
+      tma_bulk_g2s(slab + 3 * node, pr.table + di.slab3 * node, slab_bytes, bar);
+    }
   } else {
     mbar_arrive_expect_tx(bar, spec_bytes);
   }
@@ -521,21 +576,25 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
   if (q0 >= q1 || (prm.skip && *prm.skip)) return;
   const int e0 = find_event(n_events, q0, [&](int e) { return evs[e].pair_begin; });
 
-  // walk state, identical in every thread: event e, direction d, station s of pair q
+  // walk state, identical in every thread: event e, direction d, station s of pair q and the
+  // station's pattern p (see station_pattern)
   int e = e0, d, s;
   {
     const long long lq = q0 - evs[e0].pair_begin;
     d = static_cast<int>(lq / evs[e0].n_st);
     s = static_cast<int>(lq % evs[e0].n_st);
   }
+  int p = station_pattern(evs[e0], s);
   if (tid == 0) {
     mbar_init(bar, 1);
-    issue_pair_copies(evs[e0], d, s, true, sdir, slab, sspec, bar, M);
+    issue_pair_copies(evs[e0], d, s, p, true, sdir, slab, sspec, bar, M);
   }
   __syncthreads();    // barrier initialised, first direction visible
 
   int cur_e = e0 - 1;        // event of the previous pair (none yet)
   int cur_d = -1;
+  int cur_p = -3;
+  const int2* cur_binf = nullptr;   // frequency cells now in shared memory
   int pairs_in_dir = 0;
   DirInfo di;
   float2* hn = nullptr;
@@ -551,39 +610,49 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       __syncthreads();
       return;
     }
-    if (e != cur_e) {   // new event: its descriptor and frequency cells into shared memory
+    if (e != cur_e) {   // new event: its descriptor into shared memory
       copy_event(sev, evs + e, tid, T);
       __syncthreads();
-      for (int j = tid; j < M; j += T) sbinf[j] = __ldg(sev->binf + j);
+      cur_binf = nullptr;
     }
     const EventDesc& ev = *sev;
     const int S = ev.n_st;
-    if (e != cur_e || d != cur_d) {   // new direction: angular (bilinear) interpolation per frequency node
+    if (e != cur_e || d != cur_d || p != cur_p) {
+      // new direction or pattern: the pattern's frequency cells (if they changed) and the
+      // angular (bilinear) interpolation per frequency node
       di = *sdir;
-      const int n_f = ev.n_f;
-      const size_t node = static_cast<size_t>(n_f) * 4;
-      hn = reinterpret_cast<float2*>(smem_raw + SM::hn(n_f));
-      const auto bilin = [&](int x) {
-        const float2 a = slab[x], b = slab[node + x], c = slab[2 * node + x], dd = slab[3 * node + x];
-        float2 h;
-        h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
-        h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
-        return h;
-      };
-      for (int x = tid; x < n_f * 4; x += T) {
-        const int f = x >> 2, cp = x & 3;
-        const float2 h = bilin(x);
-        const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
-        hn[8 * f + cp] = h;
-        hn[8 * f + 4 + cp] = csub(h1, h);
+      if (p != -2) {
+        const PatternRef pr = pattern_ref(ev, p);
+        if (pr.binf != cur_binf) {
+          for (int j = tid; j < M; j += T) sbinf[j] = __ldg(pr.binf + j);
+          cur_binf = pr.binf;
+        }
+        const int n_f = pr.n_f;
+        const size_t node = static_cast<size_t>(n_f) * 4;
+        hn = reinterpret_cast<float2*>(smem_raw + SM::hn(ev.n_f_layout));
+        const auto bilin = [&](int x) {
+          const float2 a = slab[x], b = slab[node + x], c = slab[2 * node + x], dd = slab[3 * node + x];
+          float2 h;
+          h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+          h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+          return h;
+        };
+        for (int x = tid; x < n_f * 4; x += T) {
+          const int f = x >> 2, cp = x & 3;
+          const float2 h = bilin(x);
+          const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
+          hn[8 * f + cp] = h;
+          hn[8 * f + 4 + cp] = csub(h1, h);
+        }
       }
       cur_e = e;
       cur_d = d;
+      cur_p = p;
       __syncthreads();
     }
 
     // ---- frequency interpolation + 2x2 solve per bin ----
-    const bool valid = (di.st & kStBadDir) == 0;
+    const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
     bool sing = false;
     constexpr float kScale = 2.0f / static_cast<float>(N);
 #pragma unroll 1
@@ -631,9 +700,11 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       }
     }
     const bool dir_end = !has_next || e_next != e || d_next != d;
+    const int p_next = has_next ? station_pattern(e_next != e ? evs[e_next] : ev, s_next) : p;
     if (tid == 0 && has_next) {   // prefetch the next pair's inputs
       fence_proxy_async_smem();
-      issue_pair_copies(e_next != e ? evs[e_next] : ev, d_next, s_next, dir_end, sdir, slab, sspec, bar, M);
+      issue_pair_copies(e_next != e ? evs[e_next] : ev, d_next, s_next, p_next, dir_end || p_next != p, sdir, slab,
+                        sspec, bar, M);
     }
 
     // ---- pass 1: Q-point DFTs per (pol, r, ja) ----
@@ -763,6 +834,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     e = e_next;
     d = d_next;
     s = s_next;
+    p = p_next;
   }
   if (tid == 0) tma_bulk_wait_all();
 }

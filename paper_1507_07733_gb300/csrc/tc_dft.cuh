@@ -335,12 +335,13 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
   const long long pair = pair0 + lp;
   const int S = ev.n_st;
   const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
-  const DirInfo di = direction_cell(ev, ev.dirs[2 * d], ev.dirs[2 * d + 1]);
-  const int n_f = ev.n_f;
-  const size_t node = static_cast<size_t>(n_f) * 4;
+  PatternRef pr;
+  const DirInfo di = pair_cell(ev, d, station_pattern(ev, s), &pr);
+  const int n_f = di.pat == -2 ? 0 : pr.n_f;
+  const size_t node = static_cast<size_t>(pr.n_f) * 4;
   const auto bilin = [&](int x) {
-    const float2 a = __ldg(ev.table + di.slab0 * node + x), b = __ldg(ev.table + di.slab1 * node + x);
-    const float2 c = __ldg(ev.table + di.slab2 * node + x), dd = __ldg(ev.table + di.slab3 * node + x);
+    const float2 a = __ldg(pr.table + di.slab0 * node + x), b = __ldg(pr.table + di.slab1 * node + x);
+    const float2 c = __ldg(pr.table + di.slab2 * node + x), dd = __ldg(pr.table + di.slab3 * node + x);
     float2 h;
     h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
     h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
     hn[8 * f + 4 + cp] = csub(h1, h);
   }
   __syncthreads();
-  const bool valid = (di.st & kStBadDir) == 0;
+  const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
   bool sing = false;
   constexpr float kScale = 2.0f / static_cast<float>(N);
   const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
   for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
     const int j1 = i / kBandPhase, j2 = i % kBandPhase;
     const int j = j1 + A * j2;
-    const int2 bf = __ldg(ev.binf + j);
+    const int2 bf = __ldg(pr.binf + j);
     float2 et = make_float2(0.f, 0.f), ep = et;
     if (bf.x >= 0 && valid) {
       const float tf = __int_as_float(bf.y);

@@ -36,6 +36,13 @@ PATTERN_GRID = dict(n_zen=19, zen0_deg=0.0, dzen_deg=5.0,
                     n_az=72, az0_deg=0.0, daz_deg=5.0,
                     n_freq=51, f0_hz=30e6, df_hz=1e6)
 
+#: the paper's largest pattern (Sec. 3): 98 frequencies x 31 zenith x 49 azimuth angles. Read
+#: as zenith 0..90 deg step 3, azimuth 0..360 deg step 7.5 with the 360-degree node equal to
+#: the 0-degree one (48 distinct periodic nodes), and 98 frequencies spanning 30..80 MHz.
+LARGE_PATTERN_GRID = dict(n_zen=31, zen0_deg=0.0, dzen_deg=3.0,
+                          n_az=48, az0_deg=0.0, daz_deg=7.5,
+                          n_freq=98, f0_hz=30e6, df_hz=50e6 / 97)
+
 FS_HZ = 200e6           # AERA digitiser rate used by every workload
 STATION_SPACING_M = 236.0
 
@@ -68,9 +75,9 @@ class Pattern:
             "n_freq", "f0_hz", "df_hz")}
 
 
-def make_pattern(seed_key: int = 0, noise: float = 0.01) -> Pattern:
-    """Synthetic two-channel VEL table on the grid of ``PATTERN_GRID``."""
-    g = PATTERN_GRID
+def make_pattern(seed_key: int = 0, noise: float = 0.01, grid: dict | None = None) -> Pattern:
+    """Synthetic two-channel VEL table on ``grid`` (default ``PATTERN_GRID``)."""
+    g = PATTERN_GRID if grid is None else grid
     rng = _rng(101, seed_key)
     zen = np.deg2rad(g["zen0_deg"] + g["dzen_deg"] * np.arange(g["n_zen"]))
     az = np.deg2rad(g["az0_deg"] + g["daz_deg"] * np.arange(g["n_az"]))
@@ -233,6 +240,30 @@ def single_event(n_samples: int = 2048) -> Event:
 def direction_scan(n_stations: int = 124, n_samples: int = 2048) -> Event:
     """Direction scan: 124 stations x 2 x 2048 samples, 8 zenith x 8 azimuth directions."""
     return make_event(n_stations, n_samples, scan_directions(8, 8), seed_key=2, plane_wave=True)
+
+
+def mixed_antenna_patterns() -> list:
+    """The antenna types of the mixed-antenna workload: two on the standard grid (different
+    seeds) and one on the paper's largest grid (``LARGE_PATTERN_GRID``)."""
+    return [make_pattern(seed_key=0), make_pattern(seed_key=7), make_pattern(seed_key=8, grid=LARGE_PATTERN_GRID)]
+
+
+def station_antenna_types(n_stations: int, n_types: int = 3, seed_key: int = 9, sort: bool = True) -> np.ndarray:
+    """A seeded antenna type per station (about half type 0, 30 % type 1, 20 % type 2).
+
+    With ``sort`` the types are non-decreasing along the station index (stations grouped by
+    antenna type, the order the unfolding walks most efficiently); otherwise they are mixed.
+    """
+    rng = _rng(707, seed_key, n_stations)
+    p = np.array([0.5, 0.3, 0.2][:n_types])
+    t = rng.choice(n_types, size=n_stations, p=p / p.sum()).astype(np.int32)
+    return np.sort(t) if sort else t
+
+
+def mixed_antenna_scan(n_stations: int = 124, n_samples: int = 2048) -> Event:
+    """Mixed-antenna direction scan: the direction-scan event (124 stations x 2 x 2048
+    samples, 8 x 8 directions); ``station_antenna_types`` gives each station's antenna."""
+    return direction_scan(n_stations, n_samples)
 
 
 def uneven_stream(n_events: int = 256, seed_key: int = 4):

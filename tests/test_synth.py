@@ -47,3 +47,18 @@ def test_seeded_and_shapes():
     assert e.traces.shape == (10, 2, 2048) and e.n_dirs == 1
     s = synth.uneven_stream(256)
     assert len(s) == 256 and all(3 <= x[0] <= 124 and x[1] in (1024, 2048, 4096) and 16 <= x[2] <= 256 for x in s)
+
+
+def test_large_grid_and_antenna_types():
+    lp = FACTS["largest_pattern"]
+    big = synth.mixed_antenna_patterns()[2]
+    # the paper's 49 azimuth angles include 360 deg = 0 deg: 48 periodic nodes are stored
+    assert big.table.shape == (lp["n_zen"], lp["n_az"] - 1, lp["n_freq"], 2, 2)
+    assert abs(big.n_az * big.daz_rad - 2 * math.pi) <= 1e-12
+    assert abs(big.f0_hz + (big.n_freq - 1) * big.df_hz - 80e6) <= 1e-3
+    assert abs((big.n_zen - 1) * big.dzen_rad - math.pi / 2) <= 1e-12
+    t = synth.station_antenna_types(124)
+    assert t.dtype == np.int32 and t.shape == (124,) and set(np.unique(t)) == {0, 1, 2}
+    assert np.all(np.diff(t) >= 0)
+    u = synth.station_antenna_types(124, sort=False)
+    assert np.array_equal(np.sort(u), t) and np.any(np.diff(u) < 0)
