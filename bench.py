@@ -299,6 +299,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         precision = run_precision(binding, synth, ctx, pid, dev, stream)
     tensor_core = run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks)
+    mixed = run_mixed_antennas(binding, synth, ctx, dev, stream)
 
     batched = None
     if not args.no_batch:
@@ -336,6 +337,7 @@ def run_gpu(args):
             "reconstruction": recon,
             "precision": precision,
             "tensor_core_variant": tensor_core,
+            "mixed_antennas": mixed,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -464,6 +466,37 @@ def run_precision(binding, synth, ctx, pid, dev, stream, reps=50):
                 res[name] = row
             else:
                 res[name + "_2048"] = row
+    return res
+
+
+def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):
+    """Mixed-antenna scan: the scan event with three antenna types (two on the standard grid,
+    one on the paper's largest grid) assigned per station, grouped by type and mixed; device
+    time per call with CUDA events, in unfolds/s."""
+    import torch
+    ev = synth.mixed_antenna_scan()
+    ids = [ctx.load_pattern(p) for p in synth.mixed_antenna_patterns()]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    args = (ids[0], t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+    out, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev)
+    pairs = ev.n_stations * ev.n_dirs
+    res = {"workload": "124 stations x 64 directions x 2048 samples, antenna types 0/1 (19x72x51) and 2 "
+                       "(31x48x98, the paper's largest grid)"}
+    for name, grouped in (("grouped", True), ("mixed", False)):
+        types = synth.station_antenna_types(ev.n_stations, sort=grouped)
+        sp = t(np.asarray(ids, np.int32)[types])
+        fn = lambda: ctx.unfold(*args, ev.fs_hz, out=out, stream=stream, station_pattern=sp)
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        ctx.sync(stream)
+        ms = a.elapsed_time(b) / reps
+        res[name] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4),
+                     "types": [int((types == k).sum()) for k in range(3)]}
     return res
 
 

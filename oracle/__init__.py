@@ -59,6 +59,8 @@ def lib():
             L.orc_solve.restype = I
             L.orc_unfold_pair.argtypes = [PP, F, I, D, P, D, D, P, P, I32, P, U, P]
             L.orc_residual.argtypes = [I, P, P, D, D, D, P, P, P]
+            L.orc_peak_offset.argtypes = [I, P, I]
+            L.orc_peak_offset.restype = D
             L.orc_unfold_event.argtypes = [PP, F, I, I, D, D, F, P, P, I, P,
                                            P, P, I32, P, P, P, P, P, U, P]
             L.orc_unfold_sample.argtypes = [PP, F, I, D, F, P, P, I, I32, I32,
@@ -159,6 +161,23 @@ def residual(pos: np.ndarray, peak_time: np.ndarray, zen: float, az: float, n_re
     chi2 = np.empty(1)
     lib().orc_residual(pos.shape[0], _p(pos), _p(pt), zen, az, n_refr, _p(res), _p(t0), _p(chi2))
     return res, float(t0[0]), float(chi2[0])
+
+
+def peak_offset(env: np.ndarray, k: int) -> float:
+    """Sub-sample offset of the envelope maximum at sample k (parabola through k-1, k, k+1)."""
+    e = np.ascontiguousarray(env, dtype=np.float64)
+    return float(lib().orc_peak_offset(e.size, _p(e), int(k)))
+
+
+def fine_peak_times(envelope: np.ndarray, peak_idx: np.ndarray, t_start_ns: np.ndarray, fs_hz: float) -> np.ndarray:
+    """Refined peak times [D][S] from an event's envelopes [D][S][N] and peak indices [D][S]."""
+    D, S, N = envelope.shape
+    out = np.empty((D, S))
+    for d in range(D):
+        for s in range(S):
+            k = int(peak_idx[d, s])
+            out[d, s] = t_start_ns[s] + (k + peak_offset(envelope[d, s], k)) * (1e9 / fs_hz)
+    return out
 
 
 def unfold_event(pattern, ev, n_refr: float = 1.0, traces_out: bool = True) -> dict:

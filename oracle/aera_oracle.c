@@ -251,6 +251,24 @@ void orc_residual(int n_st, const double *pos /* [S][3] */, const double *peak_t
   *chi2 = ss;
 }
 
+/* ---- sub-sample peak (a variant: the paper times stations by the envelope maximum and
+ * says nothing finer) --------------------------------------------------------------------
+ * The parabola through (k-1, env[k-1]), (k, env[k]), (k+1, env[k+1]) has its vertex at
+ * k + delta with delta = (env[k-1] - env[k+1]) / (2 (env[k-1] - 2 env[k] + env[k+1])).
+ * Readings: delta = 0 at the two ends of the trace and where the second difference is not
+ * negative (no strict maximum); a vertex further than half a sample from k is clamped to
+ * +-1/2 (k is the sample maximum, so the true vertex of a concave fit lies within). */
+double orc_peak_offset(int n, const double *env, int k) {
+  if (k <= 0 || k >= n - 1) return 0.0;
+  double a = env[k - 1], b = env[k], c = env[k + 1];
+  double second = a - 2.0 * b + c;
+  if (!(second < 0.0)) return 0.0;
+  double delta = 0.5 * (a - c) / second;
+  if (delta > 0.5) delta = 0.5;
+  if (delta < -0.5) delta = -0.5;
+  return delta;
+}
+
 /* ---- whole event -------------------------------------------------------------------- */
 
 /* All pairs of one event. Output layouts: efield [D][S][2][N], env [D][S][N],
