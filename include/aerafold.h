@@ -117,6 +117,13 @@ typedef struct ar_outputs {
   double* t0_ns;               /* [D]                                                      */
   double* chi2;                /* [D] ns^2                                                 */
   uint32_t* status;            /* [D][S] AR_STATUS_* bits                                  */
+  double* peak_time_fine_ns;   /* [D][S] or NULL. A variant the paper does not define: the
+                                  peak time refined below the sample by the vertex of the
+                                  parabola through the envelope at the peak and its two
+                                  neighbours, t_start + (peak + delta) 1e9/fs with |delta| <=
+                                  1/2 (delta = 0 at the trace ends or without a strict
+                                  maximum), in FP64 from the FP32 envelope. When given, the
+                                  residual, t0 and chi2 use these times.                  */
 } ar_outputs;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, defaults). The context owns

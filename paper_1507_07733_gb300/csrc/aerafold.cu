@@ -49,6 +49,7 @@ struct LenTables {
 struct KernelCfg {
   size_t smem = 0;
   int grid = 0;
+  int slab_direct = 0;   // corner slabs read from L2 (when staging them would cost occupancy)
 };
 
 std::mutex g_create_mu;
@@ -306,14 +307,19 @@ ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
   auto it = ctx->unfold_cfg.find(key);
   if (it == ctx->unfold_cfg.end()) {
     KernelCfg kc;
-    kc.smem = UnfoldSmem<N_>::total(n_f);
     // the attribute belongs to the kernel, not to this configuration: set it to the largest
     // layout any pattern can need, so that no later set-up lowers it below a cached launch
     AR_CUDA(ctx, cudaFuncSetAttribute(unfold_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(UnfoldSmem<N_>::total(kMaxFreqNodes))));
-    int per_sm = 0;
+    // stage the corner slabs by TMA unless that lowers the CTAs per SM (large patterns)
+    int per_sm = 0, per_sm_direct = 0;
     AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, Layout<N_>::T,
-                                                               kc.smem));
+                                                               UnfoldSmem<N_>::total(n_f)));
+    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_>, Layout<N_>::T,
+                                                               UnfoldSmem<N_>::total(n_f, true)));
+    kc.slab_direct = per_sm_direct > per_sm ? 1 : 0;
+    if (kc.slab_direct) per_sm = per_sm_direct;
+    kc.smem = UnfoldSmem<N_>::total(n_f, kc.slab_direct != 0);
     if (per_sm < 1) return fail(ctx, AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM (smem %zu)", N_, kc.smem);
     kc.grid = per_sm * ctx->num_sms;
     AR_CUDA(ctx, cudaFuncSetAttribute(station_spectrum_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -403,6 +409,7 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.peak_idx = out->peak_idx;
   d.peak_amp = out->peak_amp;
   d.peak_time = out->peak_time_ns;
+  d.peak_fine = out->peak_time_fine_ns;
   d.status = out->status;
   d.residual = out->residual_ns;
   d.t0 = out->t0_ns;
@@ -450,8 +457,8 @@ cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cuda
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
   const long long pairs = static_cast<long long>(desc.n_st) * desc.n_dir;
   const long long grid = std::min<long long>(grid_cap, pairs);
-  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T, UnfoldSmem<N_>::total(pp.ev0.n_f_layout),
-                      stream, pp)) != cudaSuccess)
+  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T,
+                      UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0), stream, pp)) != cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[2], stream)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -465,6 +472,7 @@ ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, con
   EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
   ar_status st = attach_patterns(ctx, ev, rs.k_lo, &desc);
   if (st != AR_OK) return st;
+  desc.slab_direct = rs.kc->slab_direct;
   cudaError_t e = launch_path<N_>(ctx->d_err, desc, rs.kc->grid, stream, ctx->profiling ? ctx->ev : nullptr);
   if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
   if (ctx->profiling) {
@@ -655,6 +663,7 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   pp.wait_prior = 1;
   pp.ev0 = make_desc(b, pat.desc, pat.table, &e1, &out->last, rs.k_lo);
   if (attach_patterns(ctx, &e1, rs.k_lo, &pp.ev0) != AR_OK) return cudaErrorMemoryAllocation;
+  pp.ev0.slab_direct = rs.kc->slab_direct;
   const int S = ev->n_stations;
   const double dt_ns = 1e9 / ev->fs_hz;
   const double n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
@@ -671,7 +680,8 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
   plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
   for (int it = 1; it <= max_iter; ++it) {
-    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T, UnfoldSmem<N_>::total(pp.ev0.n_f_layout),
+    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T,
+                        UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0),
                         stream, pp)) != cudaSuccess)
       return e;
     fp.times = out->last.peak_time_ns;
@@ -756,15 +766,17 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   if (N != 1024 && N != 2048 && N != 4096)
     return fail(ctx, AR_ERR_UNSUPPORTED_N, "n_samples=%zu: supported lengths are 1024, 2048, 4096", N);
   // staging slots: 0 traces, 1 pos, 2 t_start, 3 dirs, 4 efield, 5 envelope, 6 peak_idx,
-  // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status, 13 station patterns
-  const size_t sizes[14] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
+  // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status, 13 station patterns,
+  // 14 fine peak times
+  const size_t sizes[15] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
                             D * 2 * sizeof(double), out->efield ? D * S * 2 * N * sizeof(float) : 0,
                             out->envelope ? D * S * N * sizeof(float) : 0, D * S * sizeof(int32_t),
                             D * S * sizeof(float), D * S * sizeof(double), D * S * sizeof(double),
                             D * sizeof(double), D * sizeof(double), D * S * sizeof(uint32_t),
-                            ev->station_pattern ? S * sizeof(int32_t) : 0};
-  if (ctx->stage.size() < 14) ctx->stage.resize(14, {nullptr, 0});
-  for (int i = 0; i < 14; ++i) {
+                            ev->station_pattern ? S * sizeof(int32_t) : 0,
+                            out->peak_time_fine_ns ? D * S * sizeof(double) : 0};
+  if (ctx->stage.size() < 15) ctx->stage.resize(15, {nullptr, 0});
+  for (int i = 0; i < 15; ++i) {
     if (sizes[i] > ctx->stage[i].second) {
       AR_CUDA(ctx, cudaDeviceSynchronize());
       cudaFree(ctx->stage[i].first);
@@ -797,10 +809,12 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   dout.t0_ns = static_cast<double*>(dev(10));
   dout.chi2 = static_cast<double*>(dev(11));
   dout.status = static_cast<uint32_t*>(dev(12));
+  dout.peak_time_fine_ns = out->peak_time_fine_ns ? static_cast<double*>(dev(14)) : nullptr;
   if ((st = ar_unfold(ctx, &de, &dout, stream)) != AR_OK) return st;
-  void* hosts[13] = {nullptr, nullptr, nullptr, nullptr, out->efield, out->envelope, out->peak_idx,
-                     out->peak_amp, out->peak_time_ns, out->residual_ns, out->t0_ns, out->chi2, out->status};
-  for (int i = 4; i < 13; ++i)
+  void* hosts[15] = {nullptr, nullptr, nullptr, nullptr, out->efield, out->envelope, out->peak_idx,
+                     out->peak_amp, out->peak_time_ns, out->residual_ns, out->t0_ns, out->chi2, out->status,
+                     nullptr, out->peak_time_fine_ns};
+  for (int i = 4; i < 15; ++i)
     if (hosts[i] && sizes[i]) AR_CUDA(ctx, cudaMemcpyAsync(hosts[i], dev(i), sizes[i], cudaMemcpyDeviceToHost, s));
   return ar_sync(ctx, stream);
 }
@@ -1456,6 +1470,7 @@ size_t req_state_bytes(const ar_event& ev, const ar_outputs& out) {
   if (out.efield) b += r(D * S * 2 * N * 4);
   if (out.envelope) b += r(D * S * N * 4);
   b += r(D * S * 4) * 2 + r(D * S * 8) * 2 + r(D * 8) * 2 + r(D * S * 4);
+  if (out.peak_time_fine_ns) b += r(D * S * 8);
   return b;
 }
 
@@ -1506,6 +1521,7 @@ void place_request(ar_server* sv, Request& r) {
   r.dev_out.t0_ns = reinterpret_cast<double*>(take(D * 8));
   r.dev_out.chi2 = reinterpret_cast<double*>(take(D * 8));
   r.dev_out.status = reinterpret_cast<uint32_t*>(take(D * S * 4));
+  if (r.out.peak_time_fine_ns) r.dev_out.peak_time_fine_ns = reinterpret_cast<double*>(take(D * S * 8));
 }
 
 cudaError_t copy_in(ar_server* sv, const Request& r) {
@@ -1537,7 +1553,8 @@ cudaError_t copy_out(ar_server* sv, const Request& r) {
                         {r.out.residual_ns, r.dev_out.residual_ns, D * S * 8},
                         {r.out.t0_ns, r.dev_out.t0_ns, D * 8},
                         {r.out.chi2, r.dev_out.chi2, D * 8},
-                        {r.out.status, r.dev_out.status, D * S * 4}};
+                        {r.out.status, r.dev_out.status, D * S * 4},
+                        {r.out.peak_time_fine_ns, r.dev_out.peak_time_fine_ns, D * S * 8}};
   for (const Item& it : items) {
     if (!it.h || !it.d) continue;
     cudaError_t e = cudaMemcpyAsync(it.h, it.d, it.n, cudaMemcpyDeviceToHost, sv->s_d2h);

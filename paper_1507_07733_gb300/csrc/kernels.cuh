@@ -172,6 +172,7 @@ struct EventDesc {
   int* peak_idx;           // [D][S]
   float* peak_amp;         // [D][S]
   double* peak_time;       // [D][S]
+  double* peak_fine;       // [D][S] sub-sample peak times, or null (then the residual uses peak_time)
   unsigned* status;        // [D][S]
   double* residual;        // [D][S]
   double* t0;              // [D]
@@ -191,6 +192,8 @@ struct EventDesc {
   int n_zen, n_az, n_f, n_st, n_dir, k_lo;
   int n_pats;
   int n_f_layout;          // frequency nodes the unfold kernel's shared memory is laid out for (>= any pattern's)
+  int slab_direct;         // 1: the corner slabs are read from the table in L2, not staged by TMA
+  int pad2;
 };
 
 struct BatchHeader {       // in device memory, followed by EventDesc[n_events] (16-byte aligned)
@@ -445,11 +448,27 @@ struct UnfoldSmem {
   static constexpr size_t DIR = EV + ((sizeof(EventDesc) + 15) / 16) * 16;  // 1 DirInfo
   static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // T/32 x (double, float, int) + flags
   static constexpr size_t BAR = RED + 16 * (L::T / 32) + 32;
-  static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2
-  __host__ __device__ static size_t hn(int n_f) { return SLAB + sizeof(float2) * 16 * n_f; }
-  // hn: per frequency node f, the 4 VEL entries at f and their slope to f + 1
-  __host__ __device__ static size_t total(int n_f) { return hn(n_f) + sizeof(float2) * 8 * n_f; }
+  static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2 (staged)
+  // hn: per frequency node f, the 4 VEL entries at f and their slope to f + 1. Without staged
+  // slabs (direct: the corners are read from the L2-resident table) hn starts at SLAB.
+  __host__ __device__ static size_t hn(int n_f, bool direct = false) {
+    return SLAB + (direct ? 0 : sizeof(float2) * 16 * n_f);
+  }
+  __host__ __device__ static size_t total(int n_f, bool direct = false) {
+    return hn(n_f, direct) + sizeof(float2) * 8 * n_f;
+  }
 };
+
+// Sub-sample offset of the envelope maximum at sample k: the vertex of the parabola through
+// (k-1, k, k+1), in FP64; 0 at the trace ends or without a strict maximum, clamped to +-1/2.
+__device__ __forceinline__ double peak_offset(const float* env, int n, int k) {
+  if (k <= 0 || k >= n - 1) return 0.0;
+  const double a = env[k - 1], b = env[k], c = env[k + 1];
+  const double second = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, b)), c);
+  if (!(second < 0.0)) return 0.0;
+  const double delta = __ddiv_rn(__dmul_rn(0.5, __dsub_rn(a, c)), second);
+  return fmin(0.5, fmax(-0.5, delta));
+}
 
 // Residual of direction d over all stations, by the whole CTA (FP64, deterministic order:
 // station s is handled by thread s mod T, and partial sums are combined in a fixed tree).
@@ -472,7 +491,7 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
   const double sz = sin(zen);
   const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
-  const double* tp = p.peak_time + static_cast<size_t>(d) * p.n_st;
+  const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
   double acc = 0.0;
   for (int s = threadIdx.x; s < p.n_st; s += T) {
     const double* x = p.pos + 3 * s;
@@ -520,7 +539,7 @@ __device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, in
     PatternRef pr;
     const DirInfo di = pair_cell(ev, d, p, &pr);
     *sdir = di;
-    if (p == -2) {
+    if (p == -2 || ev.slab_direct) {
       mbar_arrive_expect_tx(bar, spec_bytes);
     } else {
       const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
@@ -629,9 +648,25 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
         }
         const int n_f = pr.n_f;
         const size_t node = static_cast<size_t>(n_f) * 4;
-        hn = reinterpret_cast<float2*>(smem_raw + SM::hn(ev.n_f_layout));
+        hn = reinterpret_cast<float2*>(smem_raw + SM::hn(ev.n_f_layout, ev.slab_direct != 0));
+        const bool direct = ev.slab_direct != 0;
+        const float2* c0 = pr.table + di.slab0 * node;
+        const float2* c1 = pr.table + di.slab1 * node;
+        const float2* c2 = pr.table + di.slab2 * node;
+        const float2* c3 = pr.table + di.slab3 * node;
         const auto bilin = [&](int x) {
-          const float2 a = slab[x], b = slab[node + x], c = slab[2 * node + x], dd = slab[3 * node + x];
+          float2 a, b, c, dd;
+          if (direct) {
+            a = __ldg(c0 + x);
+            b = __ldg(c1 + x);
+            c = __ldg(c2 + x);
+            dd = __ldg(c3 + x);
+          } else {
+            a = slab[x];
+            b = slab[node + x];
+            c = slab[2 * node + x];
+            dd = slab[3 * node + x];
+          }
           float2 h;
           h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
           h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
@@ -729,6 +764,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     // exchange uses the first 16M bytes (where E was).
     const size_t pair = static_cast<size_t>(d) * S + s;
     const bool traces = ev.efield != nullptr;
+    const bool stage_env = traces || ev.peak_fine != nullptr;   // the sub-sample peak reads the envelope
     float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(A) + 16 * M);
     float bv = -1.0f;
     int bi = 0;
@@ -750,8 +786,8 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
         if (traces) {
           stage[n] = y0[ma].x;
           stage[N + n] = y1[ma].x;
-          stage[2 * N + n] = v;
         }
+        if (stage_env) stage[2 * N + n] = v;
         if (v > bv) { bv = v; bi = n; }
       });
     } else {
@@ -781,13 +817,13 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       if (pol == 0) {
         static_for<0, P / 2>([&](auto ma) {
           const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
-          if (traces) stage[2 * N + tq + TQ * ma] = v;
+          if (stage_env) stage[2 * N + tq + TQ * ma] = v;
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       } else {
         static_for<P / 2, P>([&](auto ma) {
           const float v = sqrt_approx(pw[ma] + xch[ma * TQ + tq]);
-          if (traces) stage[2 * N + tq + TQ * ma] = v;
+          if (stage_env) stage[2 * N + tq + TQ * ma] = v;
           if (v > bv) { bv = v; bi = tq + TQ * ma; }
         });
       }
@@ -817,6 +853,10 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       ev.peak_idx[pair] = bi;
       ev.peak_amp[pair] = bv;
       ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+      if (ev.peak_fine)
+        ev.peak_fine[pair] =
+            __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(stage + 2 * N, N, bi)),
+                                               ev.dt_ns));
       ev.status[pair] = di.st | (any_sing ? kStSingular : 0u);
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
         __threadfence();

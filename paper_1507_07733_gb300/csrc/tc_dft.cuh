@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_cons
       pw[n1] += cabs2(zz);
     }
   }
+  __shared__ float senv[N];   // for the sub-sample peak
   float bv = -1.f;
   int bi = 0;
 #pragma unroll
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_cons
     const int n = n2 + kSub * n1;
     const float v = sqrtf(pw[n1]);
     if (ev.envelope) ev.envelope[static_cast<size_t>(pair) * N + n] = v;
+    senv[n] = v;
     if (v > bv) { bv = v; bi = n; }
   }
   __shared__ float rv[kSub / 32];
@@ -452,6 +454,9 @@ __global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_cons
     ev.peak_idx[pair] = bi;
     ev.peak_amp[pair] = bv;
     ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+    if (ev.peak_fine)
+      ev.peak_fine[pair] =
+          __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(senv, N, bi)), ev.dt_ns));
   }
 }
 
