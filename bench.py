@@ -300,6 +300,7 @@ def run_gpu(args):
         precision = run_precision(binding, synth, ctx, pid, dev, stream)
     tensor_core = run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks)
     mixed = run_mixed_antennas(binding, synth, ctx, dev, stream)
+    refine = run_peak_refinement(binding, synth, ctx, pid, dev, stream)
 
     batched = None
     if not args.no_batch:
@@ -338,6 +339,7 @@ def run_gpu(args):
             "precision": precision,
             "tensor_core_variant": tensor_core,
             "mixed_antennas": mixed,
+            "peak_refinement": refine,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -497,6 +499,31 @@ def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):
         ms = a.elapsed_time(b) / reps
         res[name] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4),
                      "types": [int((types == k).sum()) for k in range(3)]}
+    return res
+
+
+def run_peak_refinement(binding, synth, ctx, pid, dev, stream, reps=100):
+    """The scan with sub-sample peak times requested (the residual then uses them), full
+    outputs and peaks only; device time per call with CUDA events, in unfolds/s."""
+    import torch
+    ev = synth.direction_scan()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+    pairs = ev.n_stations * ev.n_dirs
+    res = {"workload": "124 stations x 64 directions x 2048 samples, parabolic sub-sample peak times"}
+    for name, traces in (("full_outputs", True), ("peaks_only", False)):
+        out, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev, traces=traces, fine=True)
+        fn = lambda: ctx.unfold(*args, ev.fs_hz, out=out, stream=stream)
+        for _ in range(5):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        ctx.sync(stream)
+        ms = a.elapsed_time(b) / reps
+        res[name] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4)}
     return res
 
 
