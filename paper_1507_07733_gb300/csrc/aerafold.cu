@@ -451,7 +451,8 @@ cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cuda
   pp.ev0 = desc;
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, desc.n_st, L::T, SpectrumSmem<N_>::TOTAL, stream, pp)) !=
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, desc.n_st, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL,
+                      stream, pp)) !=
       cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
@@ -674,7 +675,8 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   // the station spectra, once: every iteration unfolds the same traces
   PathParams sp = pp;
   sp.skip = nullptr;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, S, L::T, SpectrumSmem<N_>::TOTAL, stream, sp)) != cudaSuccess)
+  if ((e = launch_pdl(station_spectrum_kernel<N_>, S, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream,
+                      sp)) != cudaSuccess)
     return e;
   voltage_peak_kernel<<<S, 256, 0, stream>>>(ev->traces, ev->t_start_ns, ev->n_samples, dt_ns, vidx, vtimes);
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
@@ -1127,7 +1129,8 @@ PathParams batch_params(ar_batch* b, int c, int wait_prior) {
 template <int N_>
 cudaError_t batch_station_launch(ar_batch* b, int c, cudaStream_t st) {
   using L = Layout<N_>;
-  return launch_pdl(station_spectrum_kernel<N_>, std::min(b->lim.max_stations, 4 * b->ctx->num_sms), L::T,
+  return launch_pdl(station_spectrum_kernel<N_>, std::min(b->lim.max_stations, 4 * b->ctx->num_sms),
+                    SpectrumSmem<N_>::THREADS,
                     SpectrumSmem<N_>::TOTAL, st, batch_params<N_>(b, c, 1));
 }
 

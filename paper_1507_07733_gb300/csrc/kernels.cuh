@@ -260,26 +260,61 @@ __device__ __forceinline__ void copy_event(EventDesc* dst, const EventDesc* src,
 
 // ---- K1: forward transform of the station voltages ---------------------------------------
 
+// Radices of the M-point transforms (M = N/4) of the station kernel, in stage order.
+template <int N_>
+struct StationRadix;
+template <>
+struct StationRadix<1024> { static constexpr int R0 = 4, R1 = 8, R2 = 8; };
+template <>
+struct StationRadix<2048> { static constexpr int R0 = 8, R1 = 8, R2 = 8; };
+template <>
+struct StationRadix<4096> { static constexpr int R0 = 16, R1 = 8, R2 = 8; };
+
 template <int N_>
 struct SpectrumSmem {
-  using L = Layout<N_>;
-  static constexpr size_t XS = 0;                                           // [4][M] float2
-  static constexpr size_t B = XS + sizeof(float2) * L::N;                   // [4][PLN] float2
-  static constexpr size_t TWF = B + sizeof(float2) * 4 * L::PLN;            // [Q][P] float2
-  static constexpr size_t TOTAL = TWF + sizeof(float2) * L::M;
+  static constexpr int N = N_, M = N_ / 4;
+  static constexpr int THREADS = 256;
+  static constexpr size_t X0 = 0;                                  // [4][M] float2 (ping)
+  static constexpr size_t X1 = X0 + sizeof(float2) * 4 * M;        // [4][M] float2 (pong)
+  static constexpr size_t TW = X1 + sizeof(float2) * 4 * M;        // [M] exp(-2 pi i x / M)
+  static constexpr size_t TOTAL = TW + sizeof(float2) * M;
 };
 
-// One CTA per station of the launch. Z[k] = sum_r W_N^{kr} U_r[k mod M], U_r = M-point DFT of
-// x[4m + r]; the M-point DFT is M = P * Q: input m = m1 + P m2, output k' = k2 + Q k1.
+// One Stockham stage of radix R over the four M-point transforms held in `in` ([4][M]):
+// span Ns (product of the radices already done); output in natural order after the last.
+template <int M, int R>
+__device__ __forceinline__ void stockham_stage(const float2* __restrict__ in, float2* __restrict__ out,
+                                               const float2* __restrict__ tw, int Ns, int tid, int nthreads) {
+  constexpr int MR = M / R;
+  for (int task = tid; task < 4 * MR; task += nthreads) {
+    const int sub = task / MR, j = task % MR;
+    const int k = j % Ns;
+    const float2* src = in + sub * M + j;
+    float2 v[R];
+    static_for<0, R>([&](auto q) { v[q] = src[q * MR]; });
+    if (Ns > 1) {
+      const int step = k * (M / (Ns * R));                   // twiddle exp(-2 pi i q k / (Ns R))
+      static_for<1, R>([&](auto q) { v[q] = cmul(v[q], tw[q * step]); });
+    }
+    dft<R, -1>(v);
+    float2* dst = out + sub * M + (j / Ns) * Ns * R + k;
+    static_for<0, R>([&](auto q) { dst[q * Ns] = v[q]; });
+  }
+}
+
+// One CTA per station of the launch. x[4m + r] (both channels packed as v0 + i v1) -> four
+// M-point DFTs U_r by three Stockham stages, then Z[k] = sum_r W_N^{kr} U_r[k mod M] at the
+// band bins and the split into the two channels' spectra.
 template <int N_>
-__global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(const __grid_constant__ PathParams prm) {
-  using L = Layout<N_>;
+__global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_kernel(const __grid_constant__ PathParams prm) {
   using SM = SpectrumSmem<N_>;
-  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
+  using RD = StationRadix<N_>;
+  constexpr int N = N_, M = SM::M, T = SM::THREADS;
+  static_assert(RD::R0 * RD::R1 * RD::R2 == M, "radices");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* xs = reinterpret_cast<float2*>(smem_raw + SM::XS);   // x[4m + r] at [r][m]; later U_r
-  float2* B = reinterpret_cast<float2*>(smem_raw + SM::B);
-  float2* twf = reinterpret_cast<float2*>(smem_raw + SM::TWF);
+  float2* x0 = reinterpret_cast<float2*>(smem_raw + SM::X0);   // x[4m + r] at [r][m]; later U_r
+  float2* x1 = reinterpret_cast<float2*>(smem_raw + SM::X1);
+  float2* tw = reinterpret_cast<float2*>(smem_raw + SM::TW);
   const int tid = threadIdx.x;
   pdl_launch_dependents();
   // a plain launch has one CTA per station; a batch launch walks the stations grid-stride
@@ -294,57 +329,42 @@ __global__ void __launch_bounds__(Layout<N_>::T) station_spectrum_kernel(const _
 
   const float4* v0 = reinterpret_cast<const float4*>(ev->traces + static_cast<size_t>(s) * 2 * N);
   const float4* v1 = v0 + N / 4;
-  const float2* twf_g = ev->twf;
+  const float2* wn = ev->wn;
   for (int m = tid; m < M; m += T) {
     const float4 a = __ldg(v0 + m), b = __ldg(v1 + m);
-    xs[0 * M + m] = make_float2(a.x, b.x);
-    xs[1 * M + m] = make_float2(a.y, b.y);
-    xs[2 * M + m] = make_float2(a.z, b.z);
-    xs[3 * M + m] = make_float2(a.w, b.w);
-    twf[m] = __ldg(twf_g + m);
+    x0[0 * M + m] = make_float2(a.x, b.x);
+    x0[1 * M + m] = make_float2(a.y, b.y);
+    x0[2 * M + m] = make_float2(a.z, b.z);
+    x0[3 * M + m] = make_float2(a.w, b.w);
+    tw[m] = __ldg(wn + 4 * m);                               // exp(-2 pi i m / M)
   }
   __syncthreads();
-  // pass 1: task (r, m1), Q-point DFT over m2, twiddle W_M^{m1 k2}
-  for (int task = tid; task < 4 * P; task += T) {
-    const int r = task / P, m1 = task % P;
-    float2 x[Q];
-    static_for<0, Q>([&](auto m2) { x[m2] = xs[r * M + m1 + P * m2]; });
-    dft<Q, -1>(x);
-    static_for<0, Q>([&](auto k2) {
-      if constexpr (k2 != 0) x[k2] = cmul(x[k2], twf[k2 * P + m1]);
-      B[r * PLN + m1 * LDA + k2] = x[k2];
-    });
-  }
+  stockham_stage<M, RD::R0>(x0, x1, tw, 1, tid, T);
   __syncthreads();
-  // pass 2: task (r, k2), P-point DFT over m1 -> U_r[k2 + Q k1]
-  for (int task = tid; task < 4 * Q; task += T) {
-    const int r = task / Q, k2 = task % Q;
-    float2 y[P];
-    static_for<0, P>([&](auto m1) { y[m1] = B[r * PLN + m1 * LDA + k2]; });
-    dft<P, -1>(y);
-    static_for<0, P>([&](auto k1) { xs[r * M + k2 + Q * k1] = y[k1]; });
-  }
+  stockham_stage<M, RD::R1>(x1, x0, tw, RD::R0, tid, T);
   __syncthreads();
+  stockham_stage<M, RD::R2>(x0, x1, tw, RD::R0 * RD::R1, tid, T);
+  __syncthreads();
+  const float2* U = x1;                                      // U_r[k'] at [r][k']
   // the previous kernel in the stream may still read these spectra: wait before writing them
   if (prm.wait_prior) pdl_wait_prior();
   if (s == 0)
     for (int d = tid; d < ev->n_dir; d += T) ev->dir_done[d] = 0u;
   // combine the four decimated transforms at k and N - k, split the channels
   float4* out = ev->spec + static_cast<size_t>(s) * M;
-  const float2* wn = ev->wn;
   const int k_lo = ev->k_lo;
   for (int j = tid; j < M; j += T) {
     const int k = k_lo + j;
     const int kk = k % M, km = (M - kk) % M;
     const float2 w1 = __ldg(wn + k);                      // W_N^k; W_N^{2k}, W_N^{3k} by products
     const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-    float2 z = xs[kk], zm = xs[km];
-    z = cadd(z, cmul(xs[M + kk], w1));
-    zm = cadd(zm, cmulc(xs[M + km], w1));                 // W_N^{-kr} = conj
-    z = cadd(z, cmul(xs[2 * M + kk], w2));
-    zm = cadd(zm, cmulc(xs[2 * M + km], w2));
-    z = cadd(z, cmul(xs[3 * M + kk], w3));
-    zm = cadd(zm, cmulc(xs[3 * M + km], w3));
+    float2 z = U[kk], zm = U[km];
+    z = cadd(z, cmul(U[M + kk], w1));
+    zm = cadd(zm, cmulc(U[M + km], w1));                 // W_N^{-kr} = conj
+    z = cadd(z, cmul(U[2 * M + kk], w2));
+    zm = cadd(zm, cmulc(U[2 * M + km], w2));
+    z = cadd(z, cmul(U[3 * M + kk], w3));
+    zm = cadd(zm, cmulc(U[3 * M + km], w3));
     const float2 sum = make_float2(z.x + zm.x, z.y - zm.y);   // Z[k] + conj Z[N-k]
     const float2 dif = make_float2(z.x - zm.x, z.y + zm.y);   // Z[k] - conj Z[N-k]
     out[j] = make_float4(0.5f * sum.x, 0.5f * sum.y, 0.5f * dif.y, -0.5f * dif.x);
@@ -530,10 +550,10 @@ __device__ __forceinline__ DirInfo pair_cell(const EventDesc& ev, int d, int p, 
   return di;
 }
 
-// Issue the bulk copies of one pair's inputs: the station's band spectrum and, for a new
-// (direction, pattern), the four corner slabs of the station's pattern (thread 0 only).
-__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, int p, bool new_key,
-                                                  DirInfo* sdir, float2* slab, float4* sspec, uint64_t* bar, int m) {
+// Arm the pair's mbarrier phase and, for a new (direction, pattern), issue the bulk copies of
+// the station pattern's four corner slabs (thread 0 only).
+__device__ __forceinline__ void issue_slab_copies(const EventDesc& ev, int d, int p, bool new_key, DirInfo* sdir,
+                                                  float2* slab, uint64_t* bar, int m) {
   const unsigned spec_bytes = static_cast<unsigned>(sizeof(float4)) * m;
   if (new_key) {
     PatternRef pr;
@@ -553,7 +573,17 @@ __device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, in
   } else {
     mbar_arrive_expect_tx(bar, spec_bytes);
   }
-  tma_bulk_g2s(sspec, ev.spec + static_cast<size_t>(s) * m, spec_bytes, bar);
+}
+// the station's band spectrum (thread 0 only; after issue_slab_copies armed the phase)
+__device__ __forceinline__ void issue_spec_copy(const EventDesc& ev, int s, float4* sspec, uint64_t* bar, int m) {
+  tma_bulk_g2s(sspec, ev.spec + static_cast<size_t>(s) * m, static_cast<unsigned>(sizeof(float4)) * m, bar);
+}
+// Issue the bulk copies of one pair's inputs: the station's band spectrum and, for a new
+// (direction, pattern), the four corner slabs of the station's pattern (thread 0 only).
+__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, int p, bool new_key,
+                                                  DirInfo* sdir, float2* slab, float4* sspec, uint64_t* bar, int m) {
+  issue_slab_copies(ev, d, p, new_key, sdir, slab, bar, m);
+  issue_spec_copy(ev, s, sspec, bar, m);
 }
 
 template <int N_>
@@ -587,12 +617,11 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
   const long long per = total_pairs / gridDim.x, rem = total_pairs % gridDim.x;
   const long long q0 = blockIdx.x * per + min(static_cast<long long>(blockIdx.x), rem);
   const long long q1 = q0 + per + (blockIdx.x < rem ? 1 : 0);
-  // The station spectra come from an earlier kernel: wait for the previous kernel when asked
-  // to, and let the next kernel in the stream launch only after that, so that a later kernel
-  // launched behind this one may rely on everything this one waited for.
-  if (prm.wait_prior) pdl_wait_prior();
-  pdl_launch_dependents();
-  if (q0 >= q1 || (prm.skip && *prm.skip)) return;
+  if (q0 >= q1) {
+    if (prm.wait_prior) pdl_wait_prior();
+    pdl_launch_dependents();
+    return;
+  }
   const int e0 = find_event(n_events, q0, [&](int e) { return evs[e].pair_begin; });
 
   // walk state, identical in every thread: event e, direction d, station s of pair q and the
@@ -604,9 +633,23 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     s = static_cast<int>(lq % evs[e0].n_st);
   }
   int p = station_pattern(evs[e0], s);
+  // The pattern, directions and station ids do not come from the previous kernel: the first
+  // pair's corner slabs are requested before the wait (unless a skip flag, written by the
+  // previous kernel, may cancel the whole launch).
+  const bool early = prm.skip == nullptr;
   if (tid == 0) {
     mbar_init(bar, 1);
-    issue_pair_copies(evs[e0], d, s, p, true, sdir, slab, sspec, bar, M);
+    if (early) issue_slab_copies(evs[e0], d, p, true, sdir, slab, bar, M);
+  }
+  // The station spectra come from an earlier kernel: wait for the previous kernel when asked
+  // to, and let the next kernel in the stream launch only after that, so that a later kernel
+  // launched behind this one may rely on everything this one waited for.
+  if (prm.wait_prior) pdl_wait_prior();
+  pdl_launch_dependents();
+  if (prm.skip && *prm.skip) return;   // nothing was requested in that case
+  if (tid == 0) {
+    if (early) issue_spec_copy(evs[e0], s, sspec, bar, M);
+    else issue_pair_copies(evs[e0], d, s, p, true, sdir, slab, sspec, bar, M);
   }
   __syncthreads();    // barrier initialised, first direction visible
 
