@@ -443,28 +443,33 @@ def run_precision(binding, synth, ctx, pid, dev, stream, reps=50):
     pat = synth.make_pattern()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     res = {"workload": "single event: 10 stations x 4096 samples, 1 direction (30, 45 deg)"}
+    sp = stream.cuda_stream
     for n in (4096, 2048):
         ev = synth.single_event(n)
-        args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+        keep = (t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+        es = binding.make_event(pid, *keep, ev.fs_hz)
+        out, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev)
         ref = oracle.unfold_event(pat, ev)
-        variants = [("fp32_fft", lambda: ctx.unfold(*args, ev.fs_hz, stream=stream))]
+        variants = [("fp32_fft", lambda: binding.ar_unfold(ctx.h, es, ost, sp))]
         if n == 4096:
-            variants += [("tc_split_bf16_x3", lambda: ctx.unfold_tc(*args, split_terms=3, fs_hz=ev.fs_hz, stream=stream)),
-                         ("tc_split_bf16_x6", lambda: ctx.unfold_tc(*args, split_terms=6, fs_hz=ev.fs_hz, stream=stream))]
+            variants += [("tc_split_bf16_x3", lambda: binding.ar_unfold_tc(ctx.h, es, ost, 3, sp)),
+                         ("tc_split_bf16_x6", lambda: binding.ar_unfold_tc(ctx.h, es, ost, 6, sp))]
         for name, fn in variants:
-            out = fn()
+            fn()
             ctx.sync(stream)
             row = _pair_errors({k: v.cpu().numpy() for k, v in out.items()}, ref, n)
-            if n == 4096:
-                for _ in range(5):
+            if n == 4096:   # device time per call: CUDA events around each call, median
+                for _ in range(10):
                     fn()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(reps):
+                a = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                b = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+                for i in range(reps):
+                    a[i].record(stream)
                     fn()
-                b.record(stream)
+                    b[i].record(stream)
                 ctx.sync(stream)
-                row["device_ms_per_call"] = round(a.elapsed_time(b) / reps, 4)
+                ms = sorted(x.elapsed_time(y) for x, y in zip(a, b))
+                row["device_ms_per_call"] = round(ms[len(ms) // 2], 4)
                 res[name] = row
             else:
                 res[name + "_2048"] = row
@@ -484,10 +489,12 @@ def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):
     pairs = ev.n_stations * ev.n_dirs
     res = {"workload": "124 stations x 64 directions x 2048 samples, antenna types 0/1 (19x72x51) and 2 "
                        "(31x48x98, the paper's largest grid)"}
+    ost = binding.outputs_struct(out)
     for name, grouped in (("grouped", True), ("mixed", False)):
         types = synth.station_antenna_types(ev.n_stations, sort=grouped)
         sp = t(np.asarray(ids, np.int32)[types])
-        fn = lambda: ctx.unfold(*args, ev.fs_hz, out=out, stream=stream, station_pattern=sp)
+        es = binding.make_event(*args, ev.fs_hz, 1.0, sp)
+        fn = lambda: binding.ar_unfold(ctx.h, es, ost, stream.cuda_stream)
         for _ in range(5):
             fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -511,9 +518,10 @@ def run_peak_refinement(binding, synth, ctx, pid, dev, stream, reps=100):
     args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
     pairs = ev.n_stations * ev.n_dirs
     res = {"workload": "124 stations x 64 directions x 2048 samples, parabolic sub-sample peak times"}
+    es = binding.make_event(*args, ev.fs_hz, 1.0)
     for name, traces in (("full_outputs", True), ("peaks_only", False)):
-        out, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev, traces=traces, fine=True)
-        fn = lambda: ctx.unfold(*args, ev.fs_hz, out=out, stream=stream)
+        out, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev, traces=traces, fine=True)
+        fn = lambda: binding.ar_unfold(ctx.h, es, ost, stream.cuda_stream)
         for _ in range(5):
             fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
