@@ -293,6 +293,7 @@ def run_gpu(args):
         e2e = {"value": round(pairs * world * n_e2e / el, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": n_e2e, "ms_per_step": round(el / n_e2e * 1e3, 4)}
 
+    back_to_back = run_back_to_back(binding, ctx, evs, ost, pairs, stream)
     single = run_single_event(binding, synth, ctx, pid, dev, stream)
     recon = run_reconstruction(binding, synth, ctx, pid, dev, stream)
     precision = None
@@ -334,6 +335,7 @@ def run_gpu(args):
             "kernel_ms": {"station_spectrum": round(k1, 5), "unfold_with_residual": round(k3, 5)},
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,
+            "back_to_back": back_to_back,
             "single_event": single,
             "reconstruction": recon,
             "precision": precision,
@@ -474,6 +476,24 @@ def run_precision(binding, synth, ctx, pid, dev, stream, reps=50):
             else:
                 res[name + "_2048"] = row
     return res
+
+
+def run_back_to_back(binding, ctx, es, ost, pairs, stream, reps=200):
+    """The scan called back to back on one stream, no L2 flush between calls (a stream of
+    events arriving faster than they are processed): device time per call."""
+    import torch
+    sp = stream.cuda_stream
+    for _ in range(10):
+        binding.ar_unfold(ctx.h, es, ost, sp)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        binding.ar_unfold(ctx.h, es, ost, sp)
+    b.record(stream)
+    binding.ar_sync(ctx.h, sp)
+    ms = a.elapsed_time(b) / reps
+    return {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4), "calls": reps,
+            "note": "no L2 flush between calls"}
 
 
 def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):

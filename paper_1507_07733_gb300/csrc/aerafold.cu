@@ -439,7 +439,12 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   return d;
 }
 
-// one event: the station kernel (one CTA per station), then the persistent unfold kernel
+// One event: the station kernel (one CTA per station), then the persistent unfold kernel.
+// The station kernel is launched in plain stream order: launched early behind the previous
+// call's unfold kernel it would hold SM slots that kernel's successor needs (back to back,
+// calls took 0.124 instead of 0.095 ms on the scan). The unfold kernel is launched with
+// programmatic dependent launch, so its CTAs start while the station kernel runs and fetch
+// their first corner slabs before they wait for the spectra.
 template <int N_>
 cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cudaStream_t stream,
                         cudaEvent_t* evs /* 3 events or null */) {
@@ -451,10 +456,8 @@ cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cuda
   pp.ev0 = desc;
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, desc.n_st, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL,
-                      stream, pp)) !=
-      cudaSuccess)
-    return e;
+  station_spectrum_kernel<N_><<<desc.n_st, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream>>>(pp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
   const long long pairs = static_cast<long long>(desc.n_st) * desc.n_dir;
   const long long grid = std::min<long long>(grid_cap, pairs);
