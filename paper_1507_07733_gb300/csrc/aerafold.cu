@@ -42,7 +42,6 @@ struct PatternDev {
 
 struct LenTables {
   float2* t1 = nullptr;    // [4][Q][P]
-  float2* twf = nullptr;   // [Q][P]
   float2* wn = nullptr;    // [N]
 };
 
@@ -153,20 +152,16 @@ cudaError_t upload_pretwiddles() {
 template <int N_>
 ar_status build_len_tables(ar_ctx* ctx, int k_lo, LenTables* lt) {
   using L = Layout<N_>;
-  constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P;
-  std::vector<float2> t1(4 * Q * P), twf(Q * P), wn(N);
+  constexpr int N = L::N, Q = L::Q, P = L::P;
+  std::vector<float2> t1(4 * Q * P), wn(N);
   for (int r = 0; r < 4; ++r)
     for (int mb = 0; mb < Q; ++mb)
       for (int ja = 0; ja < P; ++ja)
         t1[(r * Q + mb) * P + ja] = unit(static_cast<long>(k_lo + ja) * (r + 4 * mb), N, +1);
-  for (int q = 0; q < Q; ++q)
-    for (int p = 0; p < P; ++p) twf[q * P + p] = unit(static_cast<long>(p) * q, M, -1);
   for (int t = 0; t < N; ++t) wn[t] = unit(t, N, -1);
   AR_CUDA(ctx, cudaMalloc(&lt->t1, t1.size() * sizeof(float2)));
-  AR_CUDA(ctx, cudaMalloc(&lt->twf, twf.size() * sizeof(float2)));
   AR_CUDA(ctx, cudaMalloc(&lt->wn, wn.size() * sizeof(float2)));
   AR_CUDA(ctx, cudaMemcpy(lt->t1, t1.data(), t1.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  AR_CUDA(ctx, cudaMemcpy(lt->twf, twf.data(), twf.size() * sizeof(float2), cudaMemcpyHostToDevice));
   AR_CUDA(ctx, cudaMemcpy(lt->wn, wn.data(), wn.size() * sizeof(float2), cudaMemcpyHostToDevice));
   return AR_OK;
 }
@@ -391,7 +386,6 @@ struct PathBuffers {      // library-side buffers one launch of the path uses
   unsigned* dir_done;
   unsigned* err;
   const float2* t1;
-  const float2* twf;
   const float2* wn;
   const int2* binf;
 };
@@ -419,7 +413,6 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.table = table;
   d.binf = b.binf;
   d.t1 = b.t1;
-  d.twf = b.twf;
   d.wn = b.wn;
   d.zen0 = pd.zen0_rad;
   d.dzen = pd.dzen_rad;
@@ -472,7 +465,7 @@ template <int N_>
 ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, const Resolved& rs,
                      cudaStream_t stream) {
   const PatternDev& pat = ctx->patterns[ev->pattern_id];
-  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
   EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
   ar_status st = attach_patterns(ctx, ev, rs.k_lo, &desc);
   if (st != AR_OK) return st;
@@ -564,7 +557,6 @@ ar_status ar_destroy(ar_ctx* ctx) {
   for (auto& p : ctx->patterns) cudaFree(p.table);
   for (auto& kv : ctx->len_tables) {
     cudaFree(kv.second.t1);
-    cudaFree(kv.second.twf);
     cudaFree(kv.second.wn);
   }
   for (auto& kv : ctx->bin_tables) cudaFree(kv.second);
@@ -659,7 +651,7 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   ar_event e1 = *ev;
   e1.n_dirs = 1;
   e1.dirs_rad = st->dir;   // the direction the last fit produced (device memory)
-  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
   PathParams pp{};
   pp.batch = nullptr;
   pp.err = ctx->d_err;
@@ -1061,7 +1053,7 @@ ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, i
     ctx->tc_ws_bytes = need;
   }
   const PatternDev& pat = ctx->patterns[ev->pattern_id];
-  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
   EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
   if ((st = attach_patterns(ctx, ev, rs.k_lo, &desc)) != AR_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1206,7 +1198,7 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
                   b->lim.max_stations, dirs, b->lim.max_dirs);
     const int c = class_of(ev->n_samples);
     PathBuffers pb{reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(b->spec) + spec_off),
-                   b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->twf, rs.lt->wn, rs.binf};
+                   b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
     const PatternDev& pat = ctx->patterns[ev->pattern_id];
     EventDesc d = make_desc(pb, pat.desc, pat.table, ev, &outs[i], rs.k_lo);
     if ((st = attach_patterns(ctx, ev, rs.k_lo, &d)) != AR_OK) return st;
@@ -1826,7 +1818,7 @@ ar_status ar_server_destroy(ar_server* sv) {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 4u << 20;          // 4 MiB per device
-constexpr size_t kNoAllocTablesBytes = 112u << 10;         // err, counters, T1, TWF, WN, cells
+constexpr size_t kNoAllocTablesBytes = 112u << 10;         // err, counters, T1, WN, cells (with headroom)
 constexpr long long kNoAllocMaxStationSamples = 983040;    // stations x samples per channel
 constexpr int kNoAllocMaxDirs = 4096;                      // directions per event
 constexpr int kNoAllocMaxDevices = 64;
@@ -1866,11 +1858,11 @@ ar_status noalloc_fail(ar_status st, const char* fmt, ...) {
 // Twiddle and frequency-cell tables of one trace length, computed on the device in FP64
 // (sincospi) and rounded once to float; the same definitions as the host tables of ar_unfold.
 template <int N_>
-__global__ void noalloc_tables_kernel(float2* t1, float2* twf, float2* wn, int2* binf, int k_lo, double fs,
-                                      double f0, double df, int n_f) {
+__global__ void noalloc_tables_kernel(float2* t1, float2* wn, int2* binf, int k_lo, double fs, double f0, double df,
+                                      int n_f) {
   using L = Layout<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P;
-  const int total = 4 * Q * P + Q * P + N + M;
+  const int total = 4 * Q * P + N + M;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     double s, c;
     if (i < 4 * Q * P) {
@@ -1878,17 +1870,12 @@ __global__ void noalloc_tables_kernel(float2* t1, float2* twf, float2* wn, int2*
       const long t = (static_cast<long>(k_lo + ja) * (r + 4 * mb)) % N;
       sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
       t1[i] = make_float2(static_cast<float>(c), static_cast<float>(s));
-    } else if (i < 5 * Q * P) {
-      const int j = i - 4 * Q * P, q = j / P, p = j % P;
-      const long t = (static_cast<long>(p) * q) % M;
-      sincospi(2.0 * static_cast<double>(t) / M, &s, &c);
-      twf[j] = make_float2(static_cast<float>(c), static_cast<float>(-s));
-    } else if (i < 5 * Q * P + N) {
-      const int t = i - 5 * Q * P;
+    } else if (i < 4 * Q * P + N) {
+      const int t = i - 4 * Q * P;
       sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
       wn[t] = make_float2(static_cast<float>(c), static_cast<float>(-s));
     } else {
-      const int j = i - 5 * Q * P - N, k = k_lo + j;
+      const int j = i - 4 * Q * P - N, k = k_lo + j;
       const double f = __ddiv_rn(__dmul_rn(static_cast<double>(k), fs), static_cast<double>(N));
       if (!(f >= kBandLoHz && f <= kBandHiHz)) {
         binf[j] = make_int2(-1, 0);
@@ -1939,18 +1926,16 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
   b.err = reinterpret_cast<unsigned*>(base);
   b.dir_done = reinterpret_cast<unsigned*>(base + 256);                       // 16 KiB
   float2* t1 = reinterpret_cast<float2*>(base + 256 + (16u << 10));           // 32 KiB
-  float2* twf = reinterpret_cast<float2*>(base + 256 + (48u << 10));          // 8 KiB
-  float2* wn = reinterpret_cast<float2*>(base + 256 + (56u << 10));           // 32 KiB
-  int2* binf = reinterpret_cast<int2*>(base + 256 + (88u << 10));             // 8 KiB
+  float2* wn = reinterpret_cast<float2*>(base + 256 + (48u << 10));           // 32 KiB
+  int2* binf = reinterpret_cast<int2*>(base + 256 + (80u << 10));             // 8 KiB
   b.t1 = t1;
-  b.twf = twf;
   b.wn = wn;
   b.binf = binf;
   b.spec = reinterpret_cast<float4*>(base + kNoAllocTablesBytes);
   // the error word must start at zero (the direction counters are zeroed by the first
   // kernel); the tables are rewritten by every call
   AR_NA_CUDA(cudaMemsetAsync(b.err, 0, sizeof(unsigned), stream));
-  noalloc_tables_kernel<N_><<<40, 256, 0, stream>>>(t1, twf, wn, binf, k_lo, ev->fs_hz, pd->f0_hz, pd->df_hz,
+  noalloc_tables_kernel<N_><<<40, 256, 0, stream>>>(t1, wn, binf, k_lo, ev->fs_hz, pd->f0_hz, pd->df_hz,
                                                      pd->n_freq);
   AR_NA_CUDA(cudaGetLastError());
   int per_sm = 0;

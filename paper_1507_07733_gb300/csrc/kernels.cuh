@@ -182,7 +182,6 @@ struct EventDesc {
   const float2* table;     // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
   const int2* binf;        // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
   const float2* t1;        // [4][Q][P] pass-1 output twiddles
-  const float2* twf;       // [Q][P] forward pass twiddles exp(-2 pi i p q / M) at [q][p]
   const float2* wn;        // [N] exp(-2 pi i t / N)
   const PatternRef* pats;  // with st_pat: the loaded patterns at this (N, fs), by pattern id
   const int* st_pat;       // [S] pattern id per station, or null: every station uses the fields here
@@ -509,8 +508,10 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 template <int T>
 __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, double* red) {
   const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
-  const double sz = sin(zen);
-  const double nx = __dmul_rn(sz, cos(az)), ny = __dmul_rn(sz, sin(az)), nz = cos(zen);
+  double sz, cz, sa, ca;   // sincos: the same values as separate sin and cos, half the FP64 work
+  sincos(zen, &sz, &cz);
+  sincos(az, &sa, &ca);
+  const double nx = __dmul_rn(sz, ca), ny = __dmul_rn(sz, sa), nz = cz;
   const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
   double acc = 0.0;
   for (int s = threadIdx.x; s < p.n_st; s += T) {
