@@ -172,3 +172,31 @@ def test_batch_and_server_take_the_ids(env):
         for k, v in o.items():
             assert np.array_equal(v.numpy(), p[k]), k
     srv.close()
+
+
+def test_reconstruction_takes_the_ids(env):
+    """The iterative loop with every station's id set to one pattern equals the loop on that
+    pattern (same directions, iterations and last unfold, bit for bit)."""
+    binding, ctx, pats, ids = env
+    ev = synth.make_event(40, 2048, synth.scan_directions(1, 1), seed_key=1250)
+    args = (_dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns))
+    plain = ctx.reconstruct(ids[1], *args, ev.fs_hz, max_iter=6)
+    sp = _dev(np.full(40, ids[1], np.int32))
+    e = binding.make_event(ids[0], *args, torch.empty((1, 2), dtype=torch.float64, device="cuda"), ev.fs_hz, 1.0, sp)
+    # the binding's reconstruct builds its own event; run the ABI call directly with the ids
+    last, _ = binding.alloc_outputs(1, 40, 2048, device="cuda")
+    res = dict(direction=torch.empty(2, dtype=torch.float64, device="cuda"),
+               t0_ns=torch.empty(1, dtype=torch.float64, device="cuda"),
+               chi2=torch.empty(1, dtype=torch.float64, device="cuda"),
+               iterations=torch.empty(1, dtype=torch.int32, device="cuda"),
+               history=torch.empty((7, 2), dtype=torch.float64, device="cuda"))
+    out = binding.ar_recon_out(binding._ptr(res["direction"]), binding._ptr(res["t0_ns"]), binding._ptr(res["chi2"]),
+                               binding._ptr(res["iterations"]), binding._ptr(res["history"]),
+                               binding.outputs_struct(last))
+    st = torch.cuda.current_stream()
+    binding.ar_reconstruct(ctx.h, e, 6, 1e-6, out, st.cuda_stream)
+    binding.ar_sync(ctx.h, st.cuda_stream)
+    for k in ("direction", "t0_ns", "chi2", "iterations", "history"):
+        assert np.array_equal(np.nan_to_num(res[k].cpu().numpy()), np.nan_to_num(plain[k].cpu().numpy())), k
+    for k, v in last.items():
+        assert np.array_equal(v.cpu().numpy(), plain["last"][k].cpu().numpy()), k

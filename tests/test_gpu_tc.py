@@ -113,3 +113,25 @@ def test_peaks_only_and_argument_checks(env):
     with pytest.raises(binding.ArError) as e:
         ctx.unfold_tc(pid, tr, pos, ts, dirs, split_terms=3)
     assert e.value.status == 1
+
+
+def test_x3_and_x6_on_the_scan_in_the_benchmark_configuration(env):
+    """The direction scan (124 stations x 64 directions x 2048 samples) as the benchmark runs
+    it: x6 at the full bar and x3 at its bar on sampled pairs; every pair's peak time follows
+    its index; residuals against the oracle's residuals at the GPU's peak times."""
+    binding, ctx, pat, pid = env
+    ev = synth.direction_scan()
+    rng = np.random.default_rng(2048)
+    q = rng.choice(ev.n_stations * ev.n_dirs, 24, replace=False)
+    di, si = q // ev.n_stations, q % ev.n_stations
+    ref = oracle.unfold_sample(pat, ev, si, di)
+    for terms, bar in ((6, 1e-5), (3, X3_REL_L2)):
+        gpu = _run(ctx, pid, ev, terms)
+        e = rel_l2(gpu["efield"][di, si], ref["efield"], 2 * ev.n_samples)
+        v = rel_l2(gpu["envelope"][di, si], ref["envelope"], ev.n_samples)
+        assert e.max() <= bar and v.max() <= bar, (terms, e.max(), v.max())
+        assert np.array_equal(gpu["status"][di, si], ref["status"])
+        assert np.allclose(gpu["peak_time_ns"], ev.t_start_ns[None, :] + gpu["peak_idx"] * 5.0, rtol=0, atol=1e-9)
+        for d in range(0, ev.n_dirs, 9):
+            r, t0, chi2 = oracle.residual(ev.pos_m, gpu["peak_time_ns"][d], *ev.dirs_rad[d])
+            assert np.allclose(gpu["residual_ns"][d], r, rtol=0, atol=1e-9 * max(1.0, np.abs(r).max()))
