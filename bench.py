@@ -301,6 +301,9 @@ def run_gpu(args):
         e2e.update({"h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h})
 
     back_to_back = run_back_to_back(binding, ctx, evs, ost, pairs, stream)
+    l2_gbs = measure_l2_gbs(dev)
+    peaks_only = run_peaks_only(binding, ctx, pid, (tr, pos, ts, dirs), ev.fs_hz, D, S, N, pairs, flops, fp32_peak,
+                                l2_gbs, dev, stream)
     single = run_single_event(binding, synth, ctx, pid, dev, stream)
     recon = run_reconstruction(binding, synth, ctx, pid, dev, stream)
     precision = None
@@ -344,6 +347,8 @@ def run_gpu(args):
             "e2e": e2e,
             "e2e_synchronous": e2e_sync,
             "back_to_back": back_to_back,
+            "peaks_only": peaks_only,
+            "l2_gbs_measured": l2_gbs,
             "single_event": single,
             "reconstruction": recon,
             "precision": precision,
@@ -511,6 +516,63 @@ def run_e2e_pipelined(binding, ctx, pid, host_inputs, fs_hz, D, S, N, pairs, n, 
     return {"value": round(pairs * world * n / el, 1), "unit": UNIT, "steps": n,
             "ms_per_step": round(el / n * 1e3, 4),
             "api": "ar_submit / ar_wait (server: copies of one event overlap the next one's unfold)"}
+
+
+def measure_l2_gbs(dev, copies=200):
+    """L2 bandwidth on this GPU: device copies whose source and destination stay resident in
+    L2 (2 x 4, 8 and 16 MiB), replayed from a captured CUDA graph so that the copies run back
+    to back; read + write bytes over CUDA-event time, best size and run."""
+    import torch
+    best = 0.0
+    for mib in (4, 8, 16):
+        a = torch.empty(mib << 20, dtype=torch.uint8, device=dev).fill_(1)
+        b = torch.empty_like(a)
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            b.copy_(a)
+        torch.cuda.current_stream(dev).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(copies):
+                b.copy_(a)
+        g.replay()
+        torch.cuda.synchronize(dev)
+        for _ in range(3):
+            x, y = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.record()
+            g.replay()
+            y.record()
+            torch.cuda.synchronize(dev)
+            best = max(best, 2.0 * a.numel() * copies / (x.elapsed_time(y) * 1e-3) / 1e9)
+        del g
+    return round(best, 1)
+
+
+def run_peaks_only(binding, ctx, pid, keep, fs_hz, D, S, N, pairs, flops, fp32_peak, l2_gbs, dev, stream, reps=200):
+    """The scan in peaks-only mode (no E-field or envelope written): ALU- and L2-bound, so it
+    is reported against the FP32 peak and the measured L2 bandwidth. L2 bytes per pair: the
+    station spectrum staged by a bulk copy (4N B) and the 28 B of results."""
+    import torch
+    es = binding.make_event(pid, *keep, fs_hz, 1.0)
+    out, ost = binding.alloc_outputs(D, S, N, device=dev, traces=False)
+    sp = stream.cuda_stream
+    for _ in range(10):
+        binding.ar_unfold(ctx.h, es, ost, sp)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        binding.ar_unfold(ctx.h, es, ost, sp)
+    b.record(stream)
+    binding.ar_sync(ctx.h, sp)
+    s = a.elapsed_time(b) / reps * 1e-3
+    l2_bytes = pairs * (4 * N + 28)
+    return {"unfolds_per_s": round(pairs / s, 1), "ms_per_call": round(s * 1e3, 4),
+            "fp32": {"achieved_tflops": round(flops / s / 1e12, 2), "peak": round(fp32_peak, 1),
+                     "frac": round(flops / s / 1e12 / fp32_peak, 3)},
+            "l2": {"achieved_gbs": round(l2_bytes / s / 1e9, 1), "peak_measured_gbs": l2_gbs,
+                   "frac": round(l2_bytes / s / 1e9 / l2_gbs, 3) if l2_gbs else None},
+            "note": "back to back, two kernels per call"}
 
 
 def run_back_to_back(binding, ctx, es, ost, pairs, stream, reps=200):

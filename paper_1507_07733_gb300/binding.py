@@ -26,6 +26,7 @@ STATUS_NAMES = ["AR_OK", "AR_ERR_INVALID_ARG", "AR_ERR_UNSUPPORTED_N", "AR_ERR_N
 AR_STATUS_SINGULAR = 1
 AR_STATUS_ZEN_CLAMP = 2
 AR_STATUS_BAD_DIR = 4
+AR_STATUS_BAD_PATTERN = 8
 
 #: every symbol include/aerafold.h declares
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",

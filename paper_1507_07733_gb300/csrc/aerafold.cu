@@ -670,9 +670,8 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   // the station spectra, once: every iteration unfolds the same traces
   PathParams sp = pp;
   sp.skip = nullptr;
-  if ((e = launch_pdl(station_spectrum_kernel<N_>, S, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream,
-                      sp)) != cudaSuccess)
-    return e;
+  station_spectrum_kernel<N_><<<S, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream>>>(sp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   voltage_peak_kernel<<<S, 256, 0, stream>>>(ev->traces, ev->t_start_ns, ev->n_samples, dt_ns, vidx, vtimes);
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
   plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
