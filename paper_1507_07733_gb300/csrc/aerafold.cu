@@ -965,8 +965,12 @@ cudaError_t launch_gemm(ar_ctx* ctx, __nv_bfloat16* const (&a)[3], size_t m_pad,
   gp.chunks_per_group = gp.chunks / groups;
   gp.d = groups > 1 ? part : d;
   gp.d_group = m_pad * static_cast<size_t>(n);
-  const dim3 grid(n / tc::kBN, static_cast<unsigned>(m_pad / tc::kBM), groups);
-  tc::split_gemm_kernel<<<grid, tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
+  gp.m_tiles = static_cast<int>(m_pad / tc::kBM);
+  gp.n_tiles = n / tc::kBN;
+  gp.groups = groups;
+  // persistent: one CTA per SM (the kernel's shared memory allows one), items strided
+  const int items = tiles * groups;
+  tc::split_gemm_kernel<<<std::min(items, ctx->num_sms), tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || groups == 1) return e;
   const size_t n4 = gp.d_group / 4;

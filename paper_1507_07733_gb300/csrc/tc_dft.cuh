@@ -23,9 +23,9 @@
 // way split) or 6 (hi*hi, hi*mid, mid*hi, hi*lo, mid*mid, lo*hi from a three-way split). The
 // DFT matrices are split on the host from FP64 values.
 //
-// Tensor-core details (PTX ISA, tcgen05). A CTA computes a 128 x 128 tile of D = A B^T (A
-// row-major M x K, B row-major N x K, both K-major) over a range of 64-wide K chunks, with 6
-// warps in three roles: warp 4 stages each chunk's operands with bulk copies into one of two
+// Tensor-core details (PTX ISA, tcgen05). A persistent CTA (one per SM) computes 128 x 128
+// tiles of D = A B^T (A row-major M x K, B row-major N x K, both K-major), each over a range
+// of 64-wide K chunks, with 6 warps in three roles: warp 4 stages each chunk's operands with bulk copies into one of two
 // shared-memory stages (mbarrier full/empty pairs), warp 5 issues the tcgen05.mma
 // instructions (M 128, N 128, K 16; one per split product and K step) into tensor memory,
 // and warps 0-3 read the chunk's partial sum out of tensor memory (tcgen05.ld) and fold it
@@ -87,7 +87,21 @@ struct GemmParams {
   size_t d_group;
   unsigned* err;
   int ldd, chunks, chunks_per_group, terms;   // terms 3 or 6
+  int m_tiles, n_tiles, groups;               // work items: (m tile, n tile, K group), n fastest
 };
+
+// The work item of a persistent CTA's w-th item and the K chunks it covers.
+struct GemmItem {
+  int mt, nt, g;
+};
+__device__ __forceinline__ GemmItem gemm_item(const GemmParams& p, int w) {
+  const int it = blockIdx.x + gridDim.x * w;
+  GemmItem r;
+  r.g = it % p.groups;
+  r.nt = (it / p.groups) % p.n_tiles;
+  r.mt = it / (p.groups * p.n_tiles);
+  return r;
+}
 
 // FP32 -> BF16 parts, round to nearest at each step: x = hi + mid (+ lo)
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
@@ -159,8 +173,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   uint64_t* done = bars + 8;      // every MMA complete
   uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 9);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y, g = blockIdx.z;
-  const int kc0 = g * p.chunks_per_group, nk = p.chunks_per_group;
+  const int items = p.m_tiles * p.n_tiles * p.groups;
+  // Persistent: this CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; their chunks
+  // form one stream (chunk i of the stream is chunk i % cpg of item i / cpg), so one item's
+  // fold and store overlap the next item's copies and MMAs.
+  const int my_items = blockIdx.x < items ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int cpg = p.chunks_per_group;
+  const int nk = my_items * cpg;
   const int planes = p.terms == 6 ? 3 : 2;
 
   if (warp == 0) {
@@ -186,12 +205,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
         const int s = i & 1;
         if (i >= 2) ok = mbar_wait_bounded(&empty[s], ((i >> 1) - 1) & 1, kWaitLimitNs);
         if (!ok) break;
+        const GemmItem w = gemm_item(p, i / cpg);
+        const int kc = w.g * cpg + i % cpg;
         unsigned char* st = smem + s * kStageBytes;
         mbar_arrive_expect_tx(&full[s], 2u * planes * kBlk);
         for (int pl = 0; pl < planes; ++pl) {
-          tma_bulk_g2s(st + pl * kBlk, p.a[pl] + (static_cast<size_t>(mt) * p.chunks + kc0 + i) * (kBlk / 16), kBlk,
+          tma_bulk_g2s(st + pl * kBlk, p.a[pl] + (static_cast<size_t>(w.mt) * p.chunks + kc) * (kBlk / 16), kBlk,
                        &full[s]);
-          tma_bulk_g2s(st + (3 + pl) * kBlk, p.b[pl] + (static_cast<size_t>(nt) * p.chunks + kc0 + i) * (kBlk / 16),
+          tma_bulk_g2s(st + (3 + pl) * kBlk, p.b[pl] + (static_cast<size_t>(w.nt) * p.chunks + kc) * (kBlk / 16),
                        kBlk, &full[s]);
         }
         issued = i + 1;
@@ -234,22 +255,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
       mbar_wait_bounded(done, 0, kWaitLimitNs);   // no MMA outlives the tensor memory
     }
   } else {
-    // ---- fold warps: S = S + P[chunk % 2]; the last chunk's sum goes to global memory ----
+    // ---- fold warps: S = S + P[chunk % 2]; an item's last chunk goes to global memory ----
     const uint32_t lanes = static_cast<uint32_t>(32 * warp) << 16;
-    float* drow = p.d + g * p.d_group + static_cast<size_t>(mt * kBM + 32 * warp + lane) * p.ldd + nt * kBN;
     for (int i = 0; i < nk; ++i) {
       const int b = i & 1;
       ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ready[b], (i >> 1) & 1, kWaitLimitNs));   // warp-uniform
       if (!ok) break;
       tc_fence_after();
-      const bool last = i == nk - 1;
+      const int kl = i % cpg;
+      const bool first = kl == 0, last = kl == cpg - 1;
+      float* drow = nullptr;
+      if (last) {
+        const GemmItem w = gemm_item(p, i / cpg);
+        drow = p.d + w.g * p.d_group + static_cast<size_t>(w.mt * kBM + 32 * warp + lane) * p.ldd + w.nt * kBN;
+      }
 #pragma unroll 1
       for (int c = 0; c < kBN; c += 32) {
         uint32_t x[32], y[32];
         tmem_ld32(t_sum + kBN * (1 + b) + lanes + c, x);
-        if (i > 0) tmem_ld32(t_sum + lanes + c, y);
+        if (!first) tmem_ld32(t_sum + lanes + c, y);
         tmem_wait_ld();
-        if (i > 0) {
+        if (!first) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) x[k] = __float_as_uint(__fadd_rn(__uint_as_float(y[k]), __uint_as_float(x[k])));
         }
