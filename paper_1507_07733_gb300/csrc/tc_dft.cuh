@@ -157,10 +157,10 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 
 // Accumulation. The tensor cores' FP32 accumulator loses about 2^-26 of relative precision,
 // with a bias, at every MMA (measured: the error grows linearly with the number of MMAs into
-// one accumulator), so each 64-wide K chunk is accumulated on its own into a partial region
-// P[chunk % 2] of tensor memory, and warps 0-3 fold it into the running sum S with IEEE
-// round-to-nearest FP32 additions, in chunk order: S = (((P0 + P1) + P2) + ...). With two
-// partial regions the MMAs of one chunk overlap the fold of the previous one.
+// one accumulator), so each fold unit (one or two 64-wide K chunks) is accumulated on its own
+// into a partial region P[unit % 2] of tensor memory, and warps 0-3 fold it into the running
+// sum S with IEEE round-to-nearest FP32 additions, in order: S = (((P0 + P1) + P2) + ...).
+// With two partial regions the MMAs of one unit overlap the fold of the previous one.
 constexpr int kTmemCols = 512;   // S, P0, P1: 128 columns each, rounded up to a power of two
 
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
@@ -181,6 +181,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   const int cpg = p.chunks_per_group;
   const int nk = my_items * cpg;
   const int planes = p.terms == 6 ? 3 : 2;
+  // Chunks per fold: 2 when an item's chunk count is even (K = 128 accumulated on the tensor
+  // cores between folds), else 1.
+  const int F = cpg % 2 == 0 ? 2 : 1;
+  const int nu = nk / F;   // fold units
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
@@ -227,19 +231,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
     if (lane == 0) {
       for (int i = 0; i < nk && ok; ++i) {
         const int s = i & 1;
+        const int u = i / F, b = u & 1;              // fold unit and its partial region
+        const bool unit_first = i % F == 0, unit_last = i % F == F - 1;
         ok = mbar_wait_bounded(&full[s], (i >> 1) & 1, kWaitLimitNs);
-        if (ok && i >= 2) ok = mbar_wait_bounded(&pfree[s], ((i >> 1) - 1) & 1, kWaitLimitNs);
+        if (ok && unit_first && u >= 2) ok = mbar_wait_bounded(&pfree[b], ((u >> 1) - 1) & 1, kWaitLimitNs);
         if (!ok) break;
         tc_fence_after();
         const unsigned char* st = smem + s * kStageBytes;
-        const uint32_t dst = t_sum + kBN * (1 + s);
+        const uint32_t dst = t_sum + kBN * (1 + b);
 #pragma unroll 1
         for (int ks = 0; ks < kBK / 16; ++ks) {
 #pragma unroll 1
           for (int t = 0; t < p.terms; ++t) {
             const uint64_t ad = smem_desc(st + c_terms[t][0] * kBlk + ks * 256);
             const uint64_t bd = smem_desc(st + (3 + c_terms[t][1]) * kBlk + ks * 256);
-            const unsigned acc = (ks > 0 || t > 0) ? 1u : 0u;
+            const unsigned acc = (!unit_first || ks > 0 || t > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
@@ -247,8 +253,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
                 : "memory");
           }
         }
-        tc_commit(&empty[s]);   // the stage may be refilled
-        tc_commit(&ready[s]);   // the partial region may be folded
+        tc_commit(&empty[s]);                  // the stage may be refilled
+        if (unit_last) tc_commit(&ready[b]);   // the partial region may be folded
       }
       if (!ok) atomicOr(p.err, kErrTmaTimeout);
       tc_commit(done);
@@ -257,13 +263,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   } else {
     // ---- fold warps: S = S + P[chunk % 2]; an item's last chunk goes to global memory ----
     const uint32_t lanes = static_cast<uint32_t>(32 * warp) << 16;
-    for (int i = 0; i < nk; ++i) {
-      const int b = i & 1;
-      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ready[b], (i >> 1) & 1, kWaitLimitNs));   // warp-uniform
+    for (int u = 0; u < nu; ++u) {
+      const int b = u & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ready[b], (u >> 1) & 1, kWaitLimitNs));   // warp-uniform
       if (!ok) break;
       tc_fence_after();
+      const int i = u * F;                  // the unit's first chunk
       const int kl = i % cpg;
-      const bool first = kl == 0, last = kl == cpg - 1;
+      const bool first = kl == 0, last = kl + F == cpg;
       float* drow = nullptr;
       if (last) {
         const GemmItem w = gemm_item(p, i / cpg);
