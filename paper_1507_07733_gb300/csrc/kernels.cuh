@@ -507,11 +507,20 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 
 template <int T>
 __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, double* red) {
-  const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
-  double sz, cz, sa, ca;   // sincos: the same values as separate sin and cos, half the FP64 work
-  sincos(zen, &sz, &cz);
-  sincos(az, &sa, &ca);
-  const double nx = __dmul_rn(sz, ca), ny = __dmul_rn(sz, sa), nz = cz;
+  static_assert(T / 32 >= 3, "red holds the direction vector");
+  // the direction vector by one thread (FP64 is a small fraction of the FP32 rate), shared
+  // through red (at least 4 doubles; block_sum_fixed synchronises before reusing it)
+  if (threadIdx.x == 0) {
+    const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
+    double sz, cz, sa, ca;   // sincos: the same values as separate sin and cos, half the FP64 work
+    sincos(zen, &sz, &cz);
+    sincos(az, &sa, &ca);
+    red[0] = __dmul_rn(sz, ca);
+    red[1] = __dmul_rn(sz, sa);
+    red[2] = cz;
+  }
+  __syncthreads();
+  const double nx = red[0], ny = red[1], nz = red[2];
   const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
   double acc = 0.0;
   for (int s = threadIdx.x; s < p.n_st; s += T) {

@@ -368,8 +368,13 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
   const long long pair = pair0 + lp;
   const int S = ev.n_st;
   const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
-  PatternRef pr;
-  const DirInfo di = pair_cell(ev, d, station_pattern(ev, s), &pr);
+  // the pair's direction cell (FP64) by one thread: FP64 is a small fraction of the FP32 rate
+  __shared__ DirInfo s_di;
+  __shared__ PatternRef s_pr;
+  if (tid == 0) s_di = pair_cell(ev, d, station_pattern(ev, s), &s_pr);
+  __syncthreads();
+  const DirInfo di = s_di;
+  const PatternRef pr = s_pr;
   const int n_f = di.pat == -2 ? 0 : pr.n_f;
   const size_t node = static_cast<size_t>(pr.n_f) * 4;
   const auto bilin = [&](int x) {
