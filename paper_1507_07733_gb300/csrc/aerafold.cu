@@ -999,7 +999,8 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
-    tc::tc_solve_kernel<N_><<<np, 256, solve_smem, stream>>>(ev, reinterpret_cast<const float2*>(w.xf), zimg, p0);
+    tc::tc_solve_kernel<N_><<<(np + tc::kSolvePairs - 1) / tc::kSolvePairs, 256, solve_smem, stream>>>(
+        ev, reinterpret_cast<const float2*>(w.xf), zimg, p0, np);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[1], stream)) != cudaSuccess) return e;
     if ((e = launch_gemm(ctx, w.za, pad128(static_cast<size_t>(2 * A) * np), 1, terms, w.yi, w.part, stream)) !=

@@ -355,82 +355,100 @@ __global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_const
 }
 
 // ---- per pair: VEL interpolation and 2x2 solve (as the FP32 path) -> inverse GEMM rows ----
-// One CTA per pair of the chunk [pair0, pair0 + gridDim.x); the forward GEMM output holds
+// One CTA per kSolvePairs consecutive pairs of the chunk [pair0, pair0 + n_pairs), the
+// interpolation redone where the direction or the pattern changes; the forward GEMM output holds
 // X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2. Writes Zf as GEMM row
 // ((lp * 2 + pol) * A + j1), complex column j2, into the inverse GEMM's A image.
+constexpr int kSolvePairs = 8;   // pairs per solve CTA (consecutive: mostly one direction)
+
 template <int N_>
 __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ EventDesc ev, const float2* xf,
-                                                       const __grid_constant__ SplitImage img, long long pair0) {
+                                                       const __grid_constant__ SplitImage img, long long pair0,
+                                                       int n_pairs) {
   constexpr int N = N_, M = N / 4, A = N / kSub;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* hn = reinterpret_cast<float2*>(smem_raw);   // [n_f][8]: 4 values, 4 slopes
-  const int lp = blockIdx.x, tid = threadIdx.x;
-  const long long pair = pair0 + lp;
-  const int S = ev.n_st;
-  const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
-  // the pair's direction cell (FP64) by one thread: FP64 is a small fraction of the FP32 rate
   __shared__ DirInfo s_di;
   __shared__ PatternRef s_pr;
-  if (tid == 0) s_di = pair_cell(ev, d, station_pattern(ev, s), &s_pr);
-  __syncthreads();
-  const DirInfo di = s_di;
-  const PatternRef pr = s_pr;
-  const int n_f = di.pat == -2 ? 0 : pr.n_f;
-  const size_t node = static_cast<size_t>(pr.n_f) * 4;
-  const auto bilin = [&](int x) {
-    const float2 a = __ldg(pr.table + di.slab0 * node + x), b = __ldg(pr.table + di.slab1 * node + x);
-    const float2 c = __ldg(pr.table + di.slab2 * node + x), dd = __ldg(pr.table + di.slab3 * node + x);
-    float2 h;
-    h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
-    h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
-    return h;
-  };
-  for (int x = tid; x < n_f * 4; x += blockDim.x) {
-    const int f = x >> 2, cp = x & 3;
-    const float2 h = bilin(x);
-    const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
-    hn[8 * f + cp] = h;
-    hn[8 * f + 4 + cp] = csub(h1, h);
-  }
-  __syncthreads();
-  const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
-  bool sing = false;
+  const int tid = threadIdx.x;
+  const int S = ev.n_st;
   constexpr float kScale = 2.0f / static_cast<float>(N);
-  const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
-  const float2* x1 = x0 + A * kBandPhase;
-  for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
-    const int j1 = i / kBandPhase, j2 = i % kBandPhase;
-    const int j = j1 + A * j2;
-    const int2 bf = __ldg(pr.binf + j);
-    float2 et = make_float2(0.f, 0.f), ep = et;
-    if (bf.x >= 0 && valid) {
-      const float tf = __int_as_float(bf.y);
-      const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
-      const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
-      const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));
-      const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));
-      const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));
-      const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));
-      const float2 v0 = x0[i], v1 = x1[i];
-      const float2 det = csub(cmul(a, dd), cmul(b, c));
-      const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
-      const float dd2 = cabs2(det);
-      if (dd2 > 1e-12f * sc * sc) {
-        const float inv = kScale * rcp_approx(dd2);
-        const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
-        const float2 np = csub(cmul(a, v1), cmul(c, v0));
-        const float2 ct = cmulc(nt, det), cpp = cmulc(np, det);
-        et = make_float2(ct.x * inv, ct.y * inv);
-        ep = make_float2(cpp.x * inv, cpp.y * inv);
-      } else {
-        sing = true;
+  int cur_d = -1, cur_p = -3;
+  DirInfo di;
+  PatternRef pr;
+  for (int k = 0; k < kSolvePairs; ++k) {
+    const int lp = blockIdx.x * kSolvePairs + k;   // pair within the chunk
+    if (lp >= n_pairs) break;
+    const long long pair = pair0 + lp;
+    const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
+    const int p = station_pattern(ev, s);
+    if (d != cur_d || p != cur_p) {
+      // new direction or pattern: the cell (FP64) by one thread (FP64 is a small fraction of
+      // the FP32 rate), then the angular interpolation per frequency node
+      __syncthreads();   // the previous pair's reads of hn are done
+      if (tid == 0) s_di = pair_cell(ev, d, p, &s_pr);
+      __syncthreads();
+      di = s_di;
+      pr = s_pr;
+      const int n_f = di.pat == -2 ? 0 : pr.n_f;
+      const size_t node = static_cast<size_t>(pr.n_f) * 4;
+      const auto bilin = [&](int x) {
+        const float2 a = __ldg(pr.table + di.slab0 * node + x), b = __ldg(pr.table + di.slab1 * node + x);
+        const float2 c = __ldg(pr.table + di.slab2 * node + x), dd = __ldg(pr.table + di.slab3 * node + x);
+        float2 h;
+        h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+        h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+        return h;
+      };
+      for (int x = tid; x < n_f * 4; x += blockDim.x) {
+        const int f = x >> 2, cp = x & 3;
+        const float2 h = bilin(x);
+        const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
+        hn[8 * f + cp] = h;
+        hn[8 * f + 4 + cp] = csub(h1, h);
       }
+      __syncthreads();
+      cur_d = d;
+      cur_p = p;
     }
-    put_split(img.plane, img.planes, image_offset((lp * 2) * A + j1, 2 * j2, kInvK), et);
-    put_split(img.plane, img.planes, image_offset((lp * 2 + 1) * A + j1, 2 * j2, kInvK), ep);
+    const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
+    bool sing = false;
+    const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
+    const float2* x1 = x0 + A * kBandPhase;
+    for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
+      const int j1 = i / kBandPhase, j2 = i % kBandPhase;
+      const int j = j1 + A * j2;
+      const int2 bf = __ldg(pr.binf + j);
+      float2 et = make_float2(0.f, 0.f), ep = et;
+      if (bf.x >= 0 && valid) {
+        const float tf = __int_as_float(bf.y);
+        const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
+        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
+        const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));
+        const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));
+        const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));
+        const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));
+        const float2 v0 = x0[i], v1 = x1[i];
+        const float2 det = csub(cmul(a, dd), cmul(b, c));
+        const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
+        const float dd2 = cabs2(det);
+        if (dd2 > 1e-12f * sc * sc) {
+          const float inv = kScale * rcp_approx(dd2);
+          const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
+          const float2 np = csub(cmul(a, v1), cmul(c, v0));
+          const float2 ct = cmulc(nt, det), cpp = cmulc(np, det);
+          et = make_float2(ct.x * inv, ct.y * inv);
+          ep = make_float2(cpp.x * inv, cpp.y * inv);
+        } else {
+          sing = true;
+        }
+      }
+      put_split(img.plane, img.planes, image_offset((lp * 2) * A + j1, 2 * j2, kInvK), et);
+      put_split(img.plane, img.planes, image_offset((lp * 2 + 1) * A + j1, 2 * j2, kInvK), ep);
+    }
+    const bool any = __syncthreads_or(sing);
+    if (tid == 0) ev.status[pair] = di.st | (any ? kStSingular : 0u);
   }
-  const bool any = __syncthreads_or(sing);
-  if (tid == 0) ev.status[pair] = di.st | (any ? kStSingular : 0u);
 }
 
 // ---- inverse: twiddle, A-point DFT over the sub-block phase, band phase, envelope, peak ----
