@@ -310,8 +310,8 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         precision = run_precision(binding, synth, ctx, pid, dev, stream)
     tensor_core = run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks)
-    mixed = run_mixed_antennas(binding, synth, ctx, dev, stream)
-    refine = run_peak_refinement(binding, synth, ctx, pid, dev, stream)
+    mixed = run_mixed_antennas(binding, synth, ctx, dev, stream, peaks.get("hbm_gbs"))
+    refine = run_peak_refinement(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"))
 
     batched = None
     if not args.no_batch:
@@ -593,7 +593,7 @@ def run_back_to_back(binding, ctx, es, ost, pairs, stream, reps=200):
             "note": "no L2 flush between calls"}
 
 
-def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):
+def run_mixed_antennas(binding, synth, ctx, dev, stream, hbm=None, reps=100):
     """Mixed-antenna scan: the scan event with three antenna types (two on the standard grid,
     one on the paper's largest grid) assigned per station, grouped by type and mixed; device
     time per call with CUDA events, in unfolds/s."""
@@ -621,12 +621,15 @@ def run_mixed_antennas(binding, synth, ctx, dev, stream, reps=100):
         b.record(stream)
         ctx.sync(stream)
         ms = a.elapsed_time(b) / reps
+        nbytes = unfold_bytes_per_launch(ev.n_stations, ev.n_dirs, ev.n_samples, 98)
         res[name] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4),
-                     "types": [int((types == k).sum()) for k in range(3)]}
+                     "types": [int((types == k).sum()) for k in range(3)],
+                     "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                     "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 3) if hbm else None}
     return res
 
 
-def run_peak_refinement(binding, synth, ctx, pid, dev, stream, reps=100):
+def run_peak_refinement(binding, synth, ctx, pid, dev, stream, hbm=None, reps=100):
     """The scan with sub-sample peak times requested (the residual then uses them), full
     outputs and peaks only; device time per call with CUDA events, in unfolds/s."""
     import torch
@@ -648,7 +651,12 @@ def run_peak_refinement(binding, synth, ctx, pid, dev, stream, reps=100):
         b.record(stream)
         ctx.sync(stream)
         ms = a.elapsed_time(b) / reps
-        res[name] = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4)}
+        row = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4)}
+        if traces and hbm:
+            nbytes = unfold_bytes_per_launch(ev.n_stations, ev.n_dirs, ev.n_samples, 51) + 8 * pairs
+            row.update({"hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 3)})
+        res[name] = row
     return res
 
 
