@@ -999,8 +999,10 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
-    tc::tc_solve_kernel<N_><<<(np + tc::kSolvePairs - 1) / tc::kSolvePairs, 256, solve_smem, stream>>>(
-        ev, reinterpret_cast<const float2*>(w.xf), zimg, p0, np);
+    // several pairs per CTA share the interpolation, as long as two CTAs per SM remain
+    const int ppc = std::max(1, std::min(tc::kSolvePairsMax, np / (2 * ctx->num_sms)));
+    tc::tc_solve_kernel<N_><<<(np + ppc - 1) / ppc, 256, solve_smem, stream>>>(
+        ev, reinterpret_cast<const float2*>(w.xf), zimg, p0, np, ppc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[1], stream)) != cudaSuccess) return e;
     if ((e = launch_gemm(ctx, w.za, pad128(static_cast<size_t>(2 * A) * np), 1, terms, w.yi, w.part, stream)) !=

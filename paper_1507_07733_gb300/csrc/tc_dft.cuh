@@ -355,16 +355,16 @@ __global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_const
 }
 
 // ---- per pair: VEL interpolation and 2x2 solve (as the FP32 path) -> inverse GEMM rows ----
-// One CTA per kSolvePairs consecutive pairs of the chunk [pair0, pair0 + n_pairs), the
+// One CTA per pairs_per_cta consecutive pairs of the chunk [pair0, pair0 + n_pairs), the
 // interpolation redone where the direction or the pattern changes; the forward GEMM output holds
 // X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2. Writes Zf as GEMM row
 // ((lp * 2 + pol) * A + j1), complex column j2, into the inverse GEMM's A image.
-constexpr int kSolvePairs = 8;   // pairs per solve CTA (consecutive: mostly one direction)
+constexpr int kSolvePairsMax = 8;   // pairs per solve CTA (consecutive: mostly one direction)
 
 template <int N_>
 __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ EventDesc ev, const float2* xf,
                                                        const __grid_constant__ SplitImage img, long long pair0,
-                                                       int n_pairs) {
+                                                       int n_pairs, int pairs_per_cta) {
   constexpr int N = N_, M = N / 4, A = N / kSub;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* hn = reinterpret_cast<float2*>(smem_raw);   // [n_f][8]: 4 values, 4 slopes
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
   int cur_d = -1, cur_p = -3;
   DirInfo di;
   PatternRef pr;
-  for (int k = 0; k < kSolvePairs; ++k) {
-    const int lp = blockIdx.x * kSolvePairs + k;   // pair within the chunk
+  for (int k = 0; k < pairs_per_cta; ++k) {
+    const int lp = blockIdx.x * pairs_per_cta + k;   // pair within the chunk
     if (lp >= n_pairs) break;
     const long long pair = pair0 + lp;
     const int d = static_cast<int>(pair / S), s = static_cast<int>(pair % S);
