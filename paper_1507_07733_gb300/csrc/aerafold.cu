@@ -32,7 +32,6 @@ namespace {
 constexpr double kBandLoHz = 30e6;
 constexpr double kBandHiHz = 80e6;
 constexpr double kCMPerNs = 0.299792458;
-constexpr int kMaxFreqNodes = 256;
 
 struct PatternDev {
   ar_pattern_desc desc;

@@ -3,12 +3,14 @@
 //   station_spectrum_kernel  forward transform of each station's two channels, one complex
 //                            N-point DFT of (v0 + i v1) per station, split into the two real
 //                            channels' spectra; only the M = N/4 bins of the band window kept
-//   unfold_kernel            per (station, direction) pair: VEL interpolation (corner slabs of
-//                            the pattern staged by TMA bulk copies), 2x2 solve per bin, inverse
-//                            transform of the one-sided (analytic) spectrum, E-field, envelope,
-//                            peak; a persistent grid walks the pairs direction-major; the CTA
-//                            that finishes a direction last computes that direction's FP64
-//                            plane-wave timing residual (per-direction completion counters)
+//   unfold_kernel            per (station, direction) pair: 2x2 solve per bin, inverse transform
+//                            of the one-sided (analytic) spectrum, E-field, envelope, peak; a
+//                            persistent grid walks the pairs direction-major, and per (direction,
+//                            pattern) key the VEL interpolation and the per-bin inverse are formed
+//                            once in shared memory (corner slabs staged by TMA bulk copies or read
+//                            from L2) and applied to each of the key's stations; the CTA that
+//                            finishes a direction last computes that direction's FP64 plane-wave
+//                            timing residual (per-direction completion counters)
 //
 // Transform layout. The band holds at most M = N/4 bins, k in [k_lo, k_lo + M). The inverse
 // transform z[n] = sum_k Z[k] exp(2 pi i k n / N) is evaluated at n = 4m + r (r = 0..3) as
@@ -53,6 +55,7 @@ struct Layout : Shape<N_> {
   using S = Shape<N_>;
   static constexpr int T = 8 * S::P;                  // threads: one pass-1 task each
   static constexpr int SPLIT = T / (4 * S::Q);        // pass-2 threads per (r, mb): 1 or 2
+  static constexpr int MIN_CTAS = S::N == 1024 ? 5 : 512 / T;   // resident CTAs per SM the registers must allow
   static constexpr int LDA = S::Q + 1;                // row stride of A (float2)
   static constexpr int PLN0 = S::P * LDA;
   static constexpr int PLN = PLN0 + ((4 - PLN0 % 16) + 16) % 16;   // plane stride, == 4 mod 16
@@ -456,25 +459,26 @@ __device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, cons
   });
 }
 
+// Frequency nodes a pattern may have (the per-node interpolation scratch lives in A).
+constexpr int kMaxFreqNodes = 256;
+
 template <int N_>
 struct UnfoldSmem {
   using L = Layout<N_>;
   // byte offsets inside dynamic shared memory (all 16-byte aligned)
   static constexpr size_t A = 0;
-  static constexpr size_t SPEC = A + sizeof(float2) * L::A_F2;
-  static constexpr size_t BINF = SPEC + sizeof(float4) * L::M;
-  static constexpr size_t EV = BINF + sizeof(int2) * L::M;                  // current EventDesc
+  // per band bin the scaled inverse of the 2x2 VEL matrix of the current (direction,
+  // pattern): [2][M] float4, (h00, h01) then (h10, h11)
+  static constexpr size_t HINV = A + sizeof(float2) * L::A_F2;
+  static constexpr size_t EV = HINV + 2 * sizeof(float4) * L::M;            // current EventDesc
   static constexpr size_t DIR = EV + ((sizeof(EventDesc) + 15) / 16) * 16;  // 1 DirInfo
   static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // T/32 x (double, float, int) + flags
   static constexpr size_t BAR = RED + 16 * (L::T / 32) + 32;
-  static constexpr size_t SLAB = ((BAR + 8 + 127) / 128) * 128;         // 4 * n_f * 4 float2 (staged)
-  // hn: per frequency node f, the 4 VEL entries at f and their slope to f + 1. Without staged
-  // slabs (direct: the corners are read from the L2-resident table) hn starts at SLAB.
-  __host__ __device__ static size_t hn(int n_f, bool direct = false) {
-    return SLAB + (direct ? 0 : sizeof(float2) * 16 * n_f);
-  }
+  static constexpr size_t SLAB = BAR + 16;   // 4 * n_f * 4 float2 (staged corner slabs)
+  // the per-node values and slopes (8 float2 per node) are formed in A before the solve
+  static_assert(sizeof(float2) * L::A_F2 >= sizeof(float2) * 8 * kMaxFreqNodes, "node scratch must fit in A");
   __host__ __device__ static size_t total(int n_f, bool direct = false) {
-    return hn(n_f, direct) + sizeof(float2) * 8 * n_f;
+    return SLAB + (direct ? 0 : sizeof(float2) * 16 * n_f);
   }
 };
 
@@ -560,44 +564,113 @@ __device__ __forceinline__ DirInfo pair_cell(const EventDesc& ev, int d, int p, 
   return di;
 }
 
-// Arm the pair's mbarrier phase and, for a new (direction, pattern), issue the bulk copies of
-// the station pattern's four corner slabs (thread 0 only).
-__device__ __forceinline__ void issue_slab_copies(const EventDesc& ev, int d, int p, bool new_key, DirInfo* sdir,
-                                                  float2* slab, uint64_t* bar, int m) {
-  const unsigned spec_bytes = static_cast<unsigned>(sizeof(float4)) * m;
-  if (new_key) {
-    PatternRef pr;
-    const DirInfo di = pair_cell(ev, d, p, &pr);
-    *sdir = di;
-    if (p == -2 || ev.slab_direct) {
-      mbar_arrive_expect_tx(bar, spec_bytes);
-    } else {
-      const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
-      const size_t node = static_cast<size_t>(pr.n_f) * 4;
-      mbar_arrive_expect_tx(bar, spec_bytes + 4 * slab_bytes);
-      tma_bulk_g2s(slab + 0 * node, pr.table + di.slab0 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 1 * node, pr.table + di.slab1 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 2 * node, pr.table + di.slab2 * node, slab_bytes, bar);
-      tma_bulk_g2s(slab + 3 * node, pr.table + di.slab3 * node, slab_bytes, bar);
+// Whether a key's corner slabs are staged in shared memory by bulk copies (else read from
+// the L2-resident table when the key's inverse is built).
+__device__ __forceinline__ bool slab_staged(const EventDesc& ev, int p) { return p != -2 && !ev.slab_direct; }
+
+// For a new (direction, pattern) key (thread 0 only): the key's direction cell into sdir and,
+// when the slabs are staged, the bulk copies of the pattern's four corner slabs, completing
+// the mbarrier's current phase.
+__device__ __forceinline__ void issue_key(const EventDesc& ev, int d, int p, DirInfo* sdir, float2* slab,
+                                          uint64_t* bar) {
+  PatternRef pr;
+  const DirInfo di = pair_cell(ev, d, p, &pr);
+  *sdir = di;
+  if (!slab_staged(ev, p)) return;
+  const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
+  const size_t node = static_cast<size_t>(pr.n_f) * 4;
+  mbar_arrive_expect_tx(bar, 4 * slab_bytes);
+  tma_bulk_g2s(slab + 0 * node, pr.table + di.slab0 * node, slab_bytes, bar);
+  tma_bulk_g2s(slab + 1 * node, pr.table + di.slab1 * node, slab_bytes, bar);
+  tma_bulk_g2s(slab + 2 * node, pr.table + di.slab2 * node, slab_bytes, bar);
+  tma_bulk_g2s(slab + 3 * node, pr.table + di.slab3 * node, slab_bytes, bar);
+}
+
+// Build the per-bin inverse of a key (whole CTA; A is free): the bilinear (zenith, azimuth)
+// interpolation of the four corners per frequency node and its slope to the next node into A,
+// then per band bin the linear interpolation in frequency, the 2x2 determinant test and the
+// scaled inverse, H^-1 * 2/N (the 2/N of the one-sided inverse transform, Sec. 3), into hinv.
+// Returns whether any bin of the band was singular. Bins outside the pattern's frequency
+// range, singular bins and keys with a bad direction or pattern get a zero inverse.
+template <int N_>
+__device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const DirInfo& di, const float2* slab,
+                                              float2* hn, float4* hinv) {
+  using L = Layout<N_>;
+  constexpr int M = L::M, T = L::T, NB = M / T;
+  constexpr float kScale = 2.0f / static_cast<float>(L::N);
+  const int tid = threadIdx.x;
+  const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
+  const PatternRef pr = pattern_ref(ev, p);
+  if (valid) {
+    const int n_f = pr.n_f;
+    const size_t node = static_cast<size_t>(n_f) * 4;
+    const bool direct = ev.slab_direct != 0;
+    const float2* c0 = pr.table + di.slab0 * node;
+    const float2* c1 = pr.table + di.slab1 * node;
+    const float2* c2 = pr.table + di.slab2 * node;
+    const float2* c3 = pr.table + di.slab3 * node;
+    const auto bilin = [&](int x) {
+      float2 a, b, c, dd;
+      if (direct) {
+        a = __ldg(c0 + x);
+        b = __ldg(c1 + x);
+        c = __ldg(c2 + x);
+        dd = __ldg(c3 + x);
+      } else {
+        a = slab[x];
+        b = slab[node + x];
+        c = slab[2 * node + x];
+        dd = slab[3 * node + x];
+      }
+      float2 h;
+      h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
+      h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
+      return h;
+    };
+    for (int x = tid; x < n_f * 4; x += T) {
+      const int f = x >> 2, cp = x & 3;
+      const float2 h = bilin(x);
+      const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
+      hn[8 * f + cp] = h;
+      hn[8 * f + 4 + cp] = csub(h1, h);
     }
-  } else {
-    mbar_arrive_expect_tx(bar, spec_bytes);
   }
-}
-// the station's band spectrum (thread 0 only; after issue_slab_copies armed the phase)
-__device__ __forceinline__ void issue_spec_copy(const EventDesc& ev, int s, float4* sspec, uint64_t* bar, int m) {
-  tma_bulk_g2s(sspec, ev.spec + static_cast<size_t>(s) * m, static_cast<unsigned>(sizeof(float4)) * m, bar);
-}
-// Issue the bulk copies of one pair's inputs: the station's band spectrum and, for a new
-// (direction, pattern), the four corner slabs of the station's pattern (thread 0 only).
-__device__ __forceinline__ void issue_pair_copies(const EventDesc& ev, int d, int s, int p, bool new_key,
-                                                  DirInfo* sdir, float2* slab, float4* sspec, uint64_t* bar, int m) {
-  issue_slab_copies(ev, d, p, new_key, sdir, slab, bar, m);
-  issue_spec_copy(ev, s, sspec, bar, m);
+  __syncthreads();
+  bool sing = false;
+#pragma unroll 1
+  for (int i = 0; i < NB; ++i) {
+    const int j = tid + T * i;
+    float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
+    const int2 bf = valid ? __ldg(pr.binf + j) : make_int2(-1, 0);
+    if (bf.x >= 0) {
+      const float tf = __int_as_float(bf.y);
+      const float4* g = reinterpret_cast<const float4*>(hn + 8 * bf.x);
+      const float4 h01 = g[0], h23 = g[1], g01 = g[2], g23 = g[3];   // value, slope
+      const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));    // H0t
+      const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));    // H0p
+      const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));    // H1t
+      const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));   // H1p
+      const float2 det = csub(cmul(a, dd), cmul(b, c));
+      const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
+      const float dd2 = cabs2(det);
+      if (dd2 > 1e-12f * sc * sc) {
+        // X / det = X conj(det) / |det|^2
+        const float inv = kScale * rcp_approx(dd2);
+        const float2 x00 = cmulc(dd, det), x01 = cmulc(b, det), x10 = cmulc(c, det), x11 = cmulc(a, det);
+        h0 = make_float4(x00.x * inv, x00.y * inv, -x01.x * inv, -x01.y * inv);
+        h1 = make_float4(-x10.x * inv, -x10.y * inv, x11.x * inv, x11.y * inv);
+      } else {
+        sing = true;
+      }
+    }
+    hinv[j] = h0;
+    hinv[M + j] = h1;
+  }
+  return __syncthreads_or(sing);
 }
 
 template <int N_>
-__global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_constant__ PathParams prm) {
+__global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_kernel(const __grid_constant__ PathParams prm) {
   using L = Layout<N_>;
   using SM = UnfoldSmem<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P, T = L::T, LDA = L::LDA, PLN = L::PLN;
@@ -605,9 +678,9 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
   constexpr int NB = M / T;   // solve bins per thread
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* A = reinterpret_cast<float2*>(smem_raw + SM::A);
-  float2* E = A;   // E[pol][j], consumed by pass 1 before A is written
-  float4* sspec = reinterpret_cast<float4*>(smem_raw + SM::SPEC);
-  int2* sbinf = reinterpret_cast<int2*>(smem_raw + SM::BINF);
+  float2* E = A;    // E[pol][j], consumed by pass 1 before A is written
+  float2* hn = A;   // per-node VEL values and slopes while a key's inverse is built
+  float4* hinv = reinterpret_cast<float4*>(smem_raw + SM::HINV);
   EventDesc* sev = reinterpret_cast<EventDesc*>(smem_raw + SM::EV);
   DirInfo* sdir = reinterpret_cast<DirInfo*>(smem_raw + SM::DIR);
   double* redd = reinterpret_cast<double*>(smem_raw + SM::RED);      // T/32 doubles
@@ -642,140 +715,93 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
     d = static_cast<int>(lq / evs[e0].n_st);
     s = static_cast<int>(lq % evs[e0].n_st);
   }
-  int p = station_pattern(evs[e0], s);
-  // The pattern, directions and station ids do not come from the previous kernel: the first
-  // pair's corner slabs are requested before the wait (unless a skip flag, written by the
-  // previous kernel, may cancel the whole launch).
+  // The station spectra come from an earlier kernel; the pattern, directions and station ids
+  // do not, unless a skip flag (written by the previous kernel, which may cancel the whole
+  // launch) marks a loop whose directions the previous kernel computes. Without one, the
+  // first key's inverse is built before waiting for the previous kernel. After the wait the
+  // next kernel in the stream may launch, so that a kernel launched behind this one may rely
+  // on everything this one waited for.
   const bool early = prm.skip == nullptr;
+  if (!early) {
+    if (prm.wait_prior) pdl_wait_prior();
+    pdl_launch_dependents();
+    if (*prm.skip) return;
+  }
+  int p = station_pattern(evs[e0], s);
   if (tid == 0) {
     mbar_init(bar, 1);
-    if (early) issue_slab_copies(evs[e0], d, p, true, sdir, slab, bar, M);
+    issue_key(evs[e0], d, p, sdir, slab, bar);
   }
-  // The station spectra come from an earlier kernel: wait for the previous kernel when asked
-  // to, and let the next kernel in the stream launch only after that, so that a later kernel
-  // launched behind this one may rely on everything this one waited for.
-  if (prm.wait_prior) pdl_wait_prior();
-  pdl_launch_dependents();
-  if (prm.skip && *prm.skip) return;   // nothing was requested in that case
-  if (tid == 0) {
-    if (early) issue_spec_copy(evs[e0], s, sspec, bar, M);
-    else issue_pair_copies(evs[e0], d, s, p, true, sdir, slab, sspec, bar, M);
-  }
-  __syncthreads();    // barrier initialised, first direction visible
+  bool pending = slab_staged(evs[e0], p);   // slab copies to wait for before the next build
+  __syncthreads();    // barrier initialised, first direction cell visible
 
   int cur_e = e0 - 1;        // event of the previous pair (none yet)
   int cur_d = -1;
   int cur_p = -3;
-  const int2* cur_binf = nullptr;   // frequency cells now in shared memory
   int pairs_in_dir = 0;
   DirInfo di;
-  float2* hn = nullptr;
+  bool key_sing = false;
   unsigned phase = 0;
-  for (long long q = q0; q < q1; ++q, phase ^= 1u) {
-    const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
-    if (__syncthreads_or(!ok)) {   // a bulk copy never completed: report, give it one more bounded wait, leave
-      if (tid == 0) {
-        atomicOr(prm.err, kErrTmaTimeout);
-        mbar_wait_bounded(bar, phase, kWaitLimitNs);
-        tma_bulk_wait_all();
+  float4 vin[NB];            // the pair's station spectrum at this thread's bins (from L2)
+  const auto load_spec = [&](const EventDesc& x, int st) {
+    const float4* src = x.spec + static_cast<size_t>(st) * M + tid;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) vin[i] = __ldcg(src + T * i);
+  };
+  for (long long q = q0; q < q1; ++q) {
+    if (pending) {
+      const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
+      if (__syncthreads_or(!ok)) {   // a bulk copy never completed: report, give it one more bounded wait, leave
+        if (tid == 0) {
+          atomicOr(prm.err, kErrTmaTimeout);
+          mbar_wait_bounded(bar, phase, kWaitLimitNs);
+          tma_bulk_wait_all();
+        }
+        __syncthreads();
+        return;
       }
-      __syncthreads();
-      return;
+      phase ^= 1u;
     }
     if (e != cur_e) {   // new event: its descriptor into shared memory
       copy_event(sev, evs + e, tid, T);
       __syncthreads();
-      cur_binf = nullptr;
     }
     const EventDesc& ev = *sev;
     const int S = ev.n_st;
     if (e != cur_e || d != cur_d || p != cur_p) {
-      // new direction or pattern: the pattern's frequency cells (if they changed) and the
-      // angular (bilinear) interpolation per frequency node
+      // new direction or pattern: the inverse of every bin, shared by the key's stations. The
+      // node scratch overlays A: the previous pair's staged outputs must have left it.
       di = *sdir;
-      if (p != -2) {
-        const PatternRef pr = pattern_ref(ev, p);
-        if (pr.binf != cur_binf) {
-          for (int j = tid; j < M; j += T) sbinf[j] = __ldg(pr.binf + j);
-          cur_binf = pr.binf;
-        }
-        const int n_f = pr.n_f;
-        const size_t node = static_cast<size_t>(n_f) * 4;
-        hn = reinterpret_cast<float2*>(smem_raw + SM::hn(ev.n_f_layout, ev.slab_direct != 0));
-        const bool direct = ev.slab_direct != 0;
-        const float2* c0 = pr.table + di.slab0 * node;
-        const float2* c1 = pr.table + di.slab1 * node;
-        const float2* c2 = pr.table + di.slab2 * node;
-        const float2* c3 = pr.table + di.slab3 * node;
-        const auto bilin = [&](int x) {
-          float2 a, b, c, dd;
-          if (direct) {
-            a = __ldg(c0 + x);
-            b = __ldg(c1 + x);
-            c = __ldg(c2 + x);
-            dd = __ldg(c3 + x);
-          } else {
-            a = slab[x];
-            b = slab[node + x];
-            c = slab[2 * node + x];
-            dd = slab[3 * node + x];
-          }
-          float2 h;
-          h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
-          h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
-          return h;
-        };
-        for (int x = tid; x < n_f * 4; x += T) {
-          const int f = x >> 2, cp = x & 3;
-          const float2 h = bilin(x);
-          const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
-          hn[8 * f + cp] = h;
-          hn[8 * f + 4 + cp] = csub(h1, h);
-        }
-      }
+      if (tid == 0) tma_bulk_wait_read();
+      __syncthreads();
+      key_sing = build_inverse<N_>(ev, p, di, slab, hn, hinv);
       cur_e = e;
       cur_d = d;
       cur_p = p;
-      __syncthreads();
+    }
+    if (q == q0) {
+      if (early) {
+        if (prm.wait_prior) pdl_wait_prior();
+        pdl_launch_dependents();
+      }
+      load_spec(ev, s);
     }
 
-    // ---- frequency interpolation + 2x2 solve per bin ----
-    const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
-    bool sing = false;
-    constexpr float kScale = 2.0f / static_cast<float>(N);
-#pragma unroll 1
+    // ---- 2x2 solve per bin: E = H^-1 V ----
+#pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int j = tid + T * i;
-      const int2 bf = sbinf[j];
-      float2 et = make_float2(0.f, 0.f), ep = et;
-      if (bf.x >= 0 && valid) {
-        const float tf = __int_as_float(bf.y);
-        const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
-        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];   // value, slope
-        const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));    // H0t
-        const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));    // H0p
-        const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));    // H1t
-        const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));   // H1p
-        const float4 V = sspec[j];
-        const float2 v0 = make_float2(V.x, V.y), v1 = make_float2(V.z, V.w);
-        const float2 det = csub(cmul(a, dd), cmul(b, c));
-        const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
-        const float dd2 = cabs2(det);
-        if (dd2 > 1e-12f * sc * sc) {
-          const float inv = kScale * rcp_approx(dd2);
-          const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
-          const float2 np = csub(cmul(a, v1), cmul(c, v0));
-          const float2 ct = cmulc(nt, det), cp = cmulc(np, det);
-          et = make_float2(ct.x * inv, ct.y * inv);
-          ep = make_float2(cp.x * inv, cp.y * inv);
-        } else {
-          sing = true;
-        }
-      }
+      const float4 h0 = hinv[j], h1 = hinv[M + j];   // (h00, h01), (h10, h11)
+      const float4 v = vin[i];                       // (V0, V1)
+      float2 et, ep;
+      et.x = fmaf(h0.z, v.z, fmaf(-h0.w, v.w, fmaf(h0.x, v.x, -h0.y * v.y)));
+      et.y = fmaf(h0.z, v.w, fmaf(h0.w, v.z, fmaf(h0.x, v.y, h0.y * v.x)));
+      ep.x = fmaf(h1.z, v.z, fmaf(-h1.w, v.w, fmaf(h1.x, v.x, -h1.y * v.y)));
+      ep.y = fmaf(h1.z, v.w, fmaf(h1.w, v.z, fmaf(h1.x, v.y, h1.y * v.x)));
       E[j] = et;
       E[M + j] = ep;
     }
-    const bool any_sing = __syncthreads_or(sing);   // spectrum and slab buffers free from here
+    __syncthreads();   // E complete; the slab buffer is free from here
 
     // the next pair of this CTA: next station, else next direction, else the next event
     const bool has_next = q + 1 < q1;
@@ -788,12 +814,14 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
       }
     }
     const bool dir_end = !has_next || e_next != e || d_next != d;
-    const int p_next = has_next ? station_pattern(e_next != e ? evs[e_next] : ev, s_next) : p;
-    if (tid == 0 && has_next) {   // prefetch the next pair's inputs
+    const EventDesc& evn = e_next != e ? evs[e_next] : ev;
+    const int p_next = has_next ? station_pattern(evn, s_next) : p;
+    const bool next_key = has_next && (dir_end || p_next != p);
+    if (tid == 0 && next_key) {   // the next key's direction cell and corner slabs
       fence_proxy_async_smem();
-      issue_pair_copies(e_next != e ? evs[e_next] : ev, d_next, s_next, p_next, dir_end || p_next != p, sdir, slab,
-                        sspec, bar, M);
+      issue_key(evn, d_next, p_next, sdir, slab, bar);
     }
+    pending = next_key && slab_staged(evn, p_next);
 
     // ---- pass 1: Q-point DFTs per (pol, r, ja) ----
     {
@@ -881,6 +909,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
         });
       }
     }
+    if (has_next) load_spec(evn, s_next);   // in flight through the pair's end
     // peak: max value, lowest index on ties
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -910,7 +939,7 @@ __global__ void __launch_bounds__(Layout<N_>::T) unfold_kernel(const __grid_cons
         ev.peak_fine[pair] =
             __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(stage + 2 * N, N, bi)),
                                                ev.dt_ns));
-      ev.status[pair] = di.st | (any_sing ? kStSingular : 0u);
+      ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
         __threadfence();
         const unsigned before = atomicAdd(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
