@@ -247,6 +247,13 @@ ar_status get_pattern_refs(ar_ctx* ctx, int n, double fs, int k_lo, const Patter
   return AR_OK;
 }
 
+// Per-event workspace of the unfold path: the station band spectra ([S][N/4] float4), then
+// (256-byte aligned) the station walk order ([S] int2) used with per-station pattern ids.
+size_t walk_offset(int n, long long n_st) {
+  return (sizeof(float4) * static_cast<size_t>(n / 4) * static_cast<size_t>(n_st) + 255) / 256 * 256;
+}
+size_t spec_ws_bytes(int n, long long n_st) { return walk_offset(n, n_st) + sizeof(int2) * static_cast<size_t>(n_st); }
+
 // frequency nodes the unfold kernel lays its shared memory out for
 int layout_nf(const ar_ctx* ctx, const ar_event* ev) {
   return ev->station_pattern ? ctx->max_nf : ctx->patterns[ev->pattern_id].desc.n_freq;
@@ -261,6 +268,8 @@ ar_status attach_patterns(ar_ctx* ctx, const ar_event* ev, int k_lo, EventDesc* 
   if (st != AR_OK) return st;
   d->pats = refs;
   d->st_pat = ev->station_pattern;
+  d->st_walk = reinterpret_cast<int2*>(reinterpret_cast<unsigned char*>(d->spec) +
+                                       walk_offset(ev->n_samples, ev->n_stations));
   d->n_pats = count;
   d->n_f_layout = ctx->max_nf;
   return AR_OK;
@@ -357,7 +366,7 @@ ar_status resolve(ar_ctx* ctx, int n, double fs, int pid, int max_st, Resolved* 
        : n == 2048 ? unfold_cfg<2048>(ctx, n_f, &rs->kc)
                    : unfold_cfg<4096>(ctx, n_f, &rs->kc);
   if (st != AR_OK) return st;
-  return ensure_spec(ctx, sizeof(float4) * static_cast<size_t>(n / 4) * static_cast<size_t>(max_st));
+  return ensure_spec(ctx, spec_ws_bytes(n, max_st));
 }
 
 ar_status resolve_dirs(ar_ctx* ctx, int n_dir) { return ensure_dirs(ctx, static_cast<size_t>(n_dir)); }
@@ -1197,7 +1206,7 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
     if ((st = get_bin_table(ctx, ev->n_samples, ev->fs_hz, ev->pattern_id, rs.k_lo, &rs.binf)) != AR_OK) return st;
     stations += ev->n_stations;
     dirs += ev->n_dirs;
-    const size_t sb = sizeof(float4) * static_cast<size_t>(ev->n_samples / 4) * ev->n_stations;
+    const size_t sb = spec_ws_bytes(ev->n_samples, ev->n_stations);
     if (stations > b->lim.max_stations || dirs > b->lim.max_dirs || spec_off + sb > b->spec_bytes)
       return fail(ctx, AR_ERR_BUDGET, "events exceed the plan (stations %lld/%d, directions %lld/%d)", stations,
                   b->lim.max_stations, dirs, b->lim.max_dirs);
@@ -1234,8 +1243,8 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
   b->ctx = ctx;
   b->lim = *lim;
   b->desc_bytes = 16 + sizeof(EventDesc) * static_cast<size_t>(lim->max_events);
-  b->spec_bytes = sizeof(float4) * 1024 * static_cast<size_t>(lim->max_stations) +
-                  256 * static_cast<size_t>(lim->max_events);
+  b->spec_bytes = (sizeof(float4) * 1024 + sizeof(int2)) * static_cast<size_t>(lim->max_stations) +
+                  512 * static_cast<size_t>(lim->max_events);
   auto cleanup = [&](ar_status st) {
     ar_batch_destroy(b);
     return st;

@@ -188,6 +188,7 @@ struct EventDesc {
   const float2* wn;        // [N] exp(-2 pi i t / N)
   const PatternRef* pats;  // with st_pat: the loaded patterns at this (N, fs), by pattern id
   const int* st_pat;       // [S] pattern id per station, or null: every station uses the fields here
+  int2* st_walk;           // [S] with st_pat: (station, pattern index) in walk order, written by the station kernel
   double zen0, dzen, az0, daz, dt_ns, n_over_c;
   long long pair_begin;    // first pair of the event in the launch's flattened pair space
   int station_begin;       // first station of the event in the launch's flattened station space
@@ -234,6 +235,14 @@ __device__ __forceinline__ int station_pattern(const EventDesc& ev, int s) {
   if (!ev.st_pat) return -1;
   const int p = ev.st_pat[s];
   return (p >= 0 && p < ev.n_pats) ? p : -2;
+}
+// Station and pattern index at position k of an event's station walk. With per-station ids
+// the stations are walked grouped by pattern (stable order, unknown ids last; the station
+// kernel writes the order), so that a direction's stations of one antenna type are adjacent
+// and share one per-bin inverse.
+__device__ __forceinline__ int2 walk_station(const EventDesc& ev, int k) {
+  if (ev.st_walk) return __ldcg(ev.st_walk + k);
+  return make_int2(k, station_pattern(ev, k));
 }
 __device__ __forceinline__ PatternRef pattern_ref(const EventDesc& ev, int p) {
   if (p >= 0) return ev.pats[p];
@@ -352,6 +361,27 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
   if (prm.wait_prior) pdl_wait_prior();
   if (s == 0)
     for (int d = tid; d < ev->n_dir; d += T) ev->dir_done[d] = 0u;
+  if (ev->st_walk) {   // this station's position in the walk: stable by pattern, unknown ids last
+    const int S = ev->n_st, np = ev->n_pats;
+    const auto key = [&](int x) { const int p = station_pattern(*ev, x); return p < 0 ? np : p; };
+    const int ks = key(s);
+    int c = 0;
+    for (int x = tid; x < S; x += T) {
+      const int kx = key(x);
+      c += (kx < ks || (kx == ks && x < s)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    int* part = reinterpret_cast<int*>(x0);   // free since the last Stockham stage
+    if ((tid & 31) == 0) part[tid >> 5] = c;
+    __syncthreads();
+    if (tid == 0) {
+      int rank = 0;
+#pragma unroll
+      for (int w = 0; w < T / 32; ++w) rank += part[w];
+      ev->st_walk[rank] = make_int2(s, ks == np ? -2 : ks);
+    }
+  }
   // combine the four decimated transforms at k and N - k, split the channels
   float4* out = ev->spec + static_cast<size_t>(s) * M;
   const int k_lo = ev->k_lo;
@@ -707,27 +737,32 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
   }
   const int e0 = find_event(n_events, q0, [&](int e) { return evs[e].pair_begin; });
 
-  // walk state, identical in every thread: event e, direction d, station s of pair q and the
-  // station's pattern p (see station_pattern)
-  int e = e0, d, s;
+  // walk state, identical in every thread: event e, direction d, position k of pair q in the
+  // event's station walk, its station s and the station's pattern p (see walk_station)
+  int e = e0, d, k;
   {
     const long long lq = q0 - evs[e0].pair_begin;
     d = static_cast<int>(lq / evs[e0].n_st);
-    s = static_cast<int>(lq % evs[e0].n_st);
+    k = static_cast<int>(lq % evs[e0].n_st);
   }
-  // The station spectra come from an earlier kernel; the pattern, directions and station ids
-  // do not, unless a skip flag (written by the previous kernel, which may cancel the whole
-  // launch) marks a loop whose directions the previous kernel computes. Without one, the
-  // first key's inverse is built before waiting for the previous kernel. After the wait the
-  // next kernel in the stream may launch, so that a kernel launched behind this one may rely
-  // on everything this one waited for.
-  const bool early = prm.skip == nullptr;
+  // The station spectra and the walk order come from an earlier kernel; the pattern,
+  // directions and station ids do not, unless a skip flag (written by the previous kernel,
+  // which may cancel the whole launch) marks a loop whose directions the previous kernel
+  // computes. Without either, the first key's inverse is built before waiting for the
+  // previous kernel. After the wait the next kernel in the stream may launch, so that a kernel
+  // launched behind this one may rely on everything this one waited for.
+  const bool early = prm.skip == nullptr && evs[e0].st_walk == nullptr;
   if (!early) {
     if (prm.wait_prior) pdl_wait_prior();
     pdl_launch_dependents();
-    if (*prm.skip) return;
+    if (prm.skip && *prm.skip) return;
   }
-  int p = station_pattern(evs[e0], s);
+  int s, p;
+  {
+    const int2 w = walk_station(evs[e0], k);
+    s = w.x;
+    p = w.y;
+  }
   if (tid == 0) {
     mbar_init(bar, 1);
     issue_key(evs[e0], d, p, sdir, slab, bar);
@@ -768,6 +803,21 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     }
     const EventDesc& ev = *sev;
     const int S = ev.n_st;
+    // the next pair of this CTA: next station, else next direction, else the next event
+    const bool has_next = q + 1 < q1;
+    int e_next = e, d_next = d, k_next = k + 1;
+    if (k_next == S) {
+      k_next = 0;
+      if (++d_next == ev.n_dir) {
+        d_next = 0;
+        ++e_next;
+      }
+    }
+    const bool dir_end = !has_next || e_next != e || d_next != d;
+    const EventDesc& evn = e_next != e ? evs[e_next] : ev;
+    // (the walk order may come from the previous kernel: not read before waiting for it)
+    int2 w_next = make_int2(s, p);
+    if (has_next && !(q == q0 && early)) w_next = walk_station(evn, k_next);
     if (e != cur_e || d != cur_d || p != cur_p) {
       // new direction or pattern: the inverse of every bin, shared by the key's stations. The
       // node scratch overlays A: the previous pair's staged outputs must have left it.
@@ -785,7 +835,9 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
         pdl_launch_dependents();
       }
       load_spec(ev, s);
+      if (has_next && early) w_next = walk_station(evn, k_next);
     }
+    const int s_next = w_next.x, p_next = w_next.y;
 
     // ---- 2x2 solve per bin: E = H^-1 V ----
 #pragma unroll
@@ -803,19 +855,6 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     }
     __syncthreads();   // E complete; the slab buffer is free from here
 
-    // the next pair of this CTA: next station, else next direction, else the next event
-    const bool has_next = q + 1 < q1;
-    int e_next = e, d_next = d, s_next = s + 1;
-    if (s_next == S) {
-      s_next = 0;
-      if (++d_next == ev.n_dir) {
-        d_next = 0;
-        ++e_next;
-      }
-    }
-    const bool dir_end = !has_next || e_next != e || d_next != d;
-    const EventDesc& evn = e_next != e ? evs[e_next] : ev;
-    const int p_next = has_next ? station_pattern(evn, s_next) : p;
     const bool next_key = has_next && (dir_end || p_next != p);
     if (tid == 0 && next_key) {   // the next key's direction cell and corner slabs
       fence_proxy_async_smem();
@@ -955,6 +994,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     __syncthreads();   // A, reductions and the event copy free for the next pair
     e = e_next;
     d = d_next;
+    k = k_next;
     s = s_next;
     p = p_next;
   }

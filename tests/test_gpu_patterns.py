@@ -200,3 +200,29 @@ def test_reconstruction_takes_the_ids(env):
         assert np.array_equal(np.nan_to_num(res[k].cpu().numpy()), np.nan_to_num(plain[k].cpu().numpy())), k
     for k, v in last.items():
         assert np.array_equal(v.cpu().numpy(), plain["last"][k].cpu().numpy()), k
+
+
+def test_batch_mixes_events_with_and_without_ids(env):
+    """A batch whose CTAs walk from an event without ids (its first key is built before the
+    wait for the station kernel) into one with ids (stations walked grouped by pattern, in an
+    order the station kernel writes): bit for bit the plain calls of each event."""
+    binding, ctx, pats, ids = env
+    evs = [synth.make_event(124, 1024, synth.scan_directions(4, 4), seed_key=1260),
+           synth.make_event(100, 1024, synth.scan_directions(5, 2), seed_key=1261)]
+    sps = [None, np.asarray(ids, np.int32)[synth.station_antenna_types(100, sort=False, seed_key=31)]]
+    plain = [_run(ctx, ids[0], e, sp) for e, sp in zip(evs, sps)]
+    keep, structs, outs = [], [], []
+    for e, sp in zip(evs, sps):
+        k = (_dev(e.traces), _dev(e.pos_m), _dev(e.t_start_ns), _dev(e.dirs_rad),
+             _dev(sp) if sp is not None else None)
+        keep.append(k)
+        structs.append(binding.make_event(ids[0], *k[:4], e.fs_hz, 1.0, k[4]))
+        outs.append(binding.alloc_outputs(e.n_dirs, e.n_stations, e.n_samples, device="cuda")[0])
+    b = ctx.batch(2, 224, 32, max_n_freq=128)
+    for _ in range(2):   # a replay reuses the walk workspace
+        b.run(structs, outs)
+        torch.cuda.synchronize()
+        for o, p in zip(outs, plain):
+            for k, v in o.items():
+                assert np.array_equal(v.cpu().numpy(), p[k]), k
+    b.close()
