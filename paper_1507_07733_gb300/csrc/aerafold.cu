@@ -1118,6 +1118,7 @@ struct ar_batch {
   int next = 0;
   int ctas_per_sm[kClasses] = {0, 0, 0};       // chosen unfold occupancy per class
   int max_ctas_per_sm[kClasses] = {0, 0, 0};
+  int slab_direct[kClasses] = {0, 0, 0};       // corner slabs read from L2 where staging them costs occupancy
   bool tuned = false;
   float tune_ms[5] = {0, 0, 0, 0, 0};          // graph time per candidate (autotune)
 };
@@ -1149,7 +1150,8 @@ template <int N_>
 cudaError_t batch_unfold_launch(ar_batch* b, int c, int ctas_per_sm, int wait_prior, cudaStream_t st) {
   using L = Layout<N_>;
   return launch_pdl(unfold_kernel<N_>, ctas_per_sm * b->ctx->num_sms, L::T,
-                    UnfoldSmem<N_>::total(b->lim.max_n_freq), st, batch_params<N_>(b, c, wait_prior));
+                    UnfoldSmem<N_>::total(b->lim.max_n_freq, b->slab_direct[c] != 0), st,
+                    batch_params<N_>(b, c, wait_prior));
 }
 
 // capture the whole launch (descriptor copies, then per class the two kernels) into graph g
@@ -1217,6 +1219,7 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
     EventDesc d = make_desc(pb, pat.desc, pat.table, ev, &outs[i], rs.k_lo);
     if ((st = attach_patterns(ctx, ev, rs.k_lo, &d)) != AR_OK) return st;
     d.n_f_layout = b->lim.max_n_freq;   // the plan's shared-memory layout
+    d.slab_direct = b->slab_direct[c];
     d.pair_begin = hdr[c]->total_pairs;
     d.station_begin = hdr[c]->total_stations;
     dsc[c][hdr[c]->n_events++] = d;
@@ -1265,9 +1268,11 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
                      : c == 1 ? reinterpret_cast<const void*>(unfold_kernel<2048>)
                               : reinterpret_cast<const void*>(unfold_kernel<4096>);
     const int threads = c == 0 ? Layout<1024>::T : c == 1 ? Layout<2048>::T : Layout<4096>::T;
-    const size_t smem = c == 0 ? UnfoldSmem<1024>::total(lim->max_n_freq)
-                        : c == 1 ? UnfoldSmem<2048>::total(lim->max_n_freq)
-                                 : UnfoldSmem<4096>::total(lim->max_n_freq);
+    const auto smem_of = [&](bool direct) {
+      return c == 0 ? UnfoldSmem<1024>::total(lim->max_n_freq, direct)
+             : c == 1 ? UnfoldSmem<2048>::total(lim->max_n_freq, direct)
+                      : UnfoldSmem<4096>::total(lim->max_n_freq, direct);
+    };
     const size_t sp_smem = c == 0 ? SpectrumSmem<1024>::TOTAL : c == 1 ? SpectrumSmem<2048>::TOTAL : SpectrumSmem<4096>::TOTAL;
     const void* sfn = c == 0 ? reinterpret_cast<const void*>(station_spectrum_kernel<1024>)
                       : c == 1 ? reinterpret_cast<const void*>(station_spectrum_kernel<2048>)
@@ -1278,8 +1283,16 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max))) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp_smem))) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas_per_sm[c], fn, threads, smem)) != cudaSuccess)
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas_per_sm[c], fn, threads, smem_of(false))) !=
+            cudaSuccess)
       return cleanup(fail(ctx, AR_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e)));
+    int per_sm_direct = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, fn, threads, smem_of(true))) != cudaSuccess)
+      return cleanup(fail(ctx, AR_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e)));
+    if (per_sm_direct > b->max_ctas_per_sm[c]) {
+      b->slab_direct[c] = 1;
+      b->max_ctas_per_sm[c] = per_sm_direct;
+    }
     if (b->max_ctas_per_sm[c] < 1) return cleanup(fail(ctx, AR_ERR_CUDA, "unfold kernel does not fit an SM"));
     b->ctas_per_sm[c] = b->max_ctas_per_sm[c];
   }
@@ -1952,11 +1965,17 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
   noalloc_tables_kernel<N_><<<40, 256, 0, stream>>>(t1, wn, binf, k_lo, ev->fs_hz, pd->f0_hz, pd->df_hz,
                                                      pd->n_freq);
   AR_NA_CUDA(cudaGetLastError());
-  int per_sm = 0;
+  int per_sm = 0, per_sm_direct = 0;
   AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T,
                                                            UnfoldSmem<N_>::total(pd->n_freq)));
+  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_>, L::T,
+                                                           UnfoldSmem<N_>::total(pd->n_freq, true)));
+  EventDesc desc = make_desc(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo);
+  if (per_sm_direct > per_sm) {   // corner slabs read from L2 where staging them costs occupancy
+    desc.slab_direct = 1;
+    per_sm = per_sm_direct;
+  }
   if (per_sm < 1) return noalloc_fail(AR_ERR_CUDA, "unfold kernel N=%d does not fit an SM", N_);
-  const EventDesc desc = make_desc(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo);
   AR_NA_CUDA(launch_path<N_>(b.err, desc, per_sm * nd.num_sms, stream, nullptr));
   return AR_OK;
 }
