@@ -10,9 +10,10 @@ x 8), the 19 x 72 x 51 synthetic VEL table -- unfolded pair by pair through the 
   value        pairs / s over the K timed steps (device time, CUDA events per step on the
                launching stream, L2 flushed by a 256 MiB write between steps, outside the
                step's events), summed over ranks; max over ranks of the time
-  e2e          the same metric through ar_unfold_host with pinned host buffers: the inputs'
-               host->device copy, the kernels, and the device->host copy of every output
-               inside each timed step (host wall clock)
+  e2e          the same metric through the serving API (ar_submit / ar_wait) with pinned host
+               buffers: the inputs' host->device copy, the kernels, and the device->host copy
+               of every output inside the timed region (host wall clock; one event's copies
+               overlap the next one's kernels); e2e_synchronous through ar_unfold_host
   roofline     the fused unfold kernel: algorithmic bytes per launch / its mean duration
                (CUDA events recorded by the library around it, same stream) vs measured HBM;
                roofline_alu the same duration against the FP32 issue peak
@@ -311,7 +312,8 @@ def run_gpu(args):
         precision = run_precision(binding, synth, ctx, pid, dev, stream)
     tensor_core = run_tensor_core(binding, synth, ctx, pid, dev, stream, peaks)
     mixed = run_mixed_antennas(binding, synth, ctx, dev, stream, peaks.get("hbm_gbs"))
-    refine = run_peak_refinement(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"))
+    refine = run_output_variant(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"), "fine")
+    weighted = run_output_variant(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"), "snr")
 
     batched = None
     if not args.no_batch:
@@ -355,6 +357,7 @@ def run_gpu(args):
             "tensor_core_variant": tensor_core,
             "mixed_antennas": mixed,
             "peak_refinement": refine,
+            "snr_weighting": weighted,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -629,18 +632,22 @@ def run_mixed_antennas(binding, synth, ctx, dev, stream, hbm=None, reps=100):
     return res
 
 
-def run_peak_refinement(binding, synth, ctx, pid, dev, stream, hbm=None, reps=100):
-    """The scan with sub-sample peak times requested (the residual then uses them), full
-    outputs and peaks only; device time per call with CUDA events, in unfolds/s."""
+def run_output_variant(binding, synth, ctx, pid, dev, stream, hbm=None, variant="fine", reps=100):
+    """The scan with a variant output requested, full outputs and peaks only; device time per
+    call with CUDA events, in unfolds/s. ``fine``: sub-sample peak times (the residual then
+    uses them); ``snr``: pulse SNRs (the residual then weights stations by them)."""
     import torch
     ev = synth.direction_scan()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     args = (pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
     pairs = ev.n_stations * ev.n_dirs
-    res = {"workload": "124 stations x 64 directions x 2048 samples, parabolic sub-sample peak times"}
+    what = {"fine": ("parabolic sub-sample peak times", 8), "snr": ("pulse SNR and SNR-weighted residuals", 4)}
+    text, extra = what[variant]
+    res = {"workload": "124 stations x 64 directions x 2048 samples, " + text}
     es = binding.make_event(*args, ev.fs_hz, 1.0)
     for name, traces in (("full_outputs", True), ("peaks_only", False)):
-        out, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev, traces=traces, fine=True)
+        out, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev, traces=traces,
+                                         **{variant: True})
         fn = lambda: binding.ar_unfold(ctx.h, es, ost, stream.cuda_stream)
         for _ in range(5):
             fn()
@@ -653,7 +660,7 @@ def run_peak_refinement(binding, synth, ctx, pid, dev, stream, hbm=None, reps=10
         ms = a.elapsed_time(b) / reps
         row = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4)}
         if traces and hbm:
-            nbytes = unfold_bytes_per_launch(ev.n_stations, ev.n_dirs, ev.n_samples, 51) + 8 * pairs
+            nbytes = unfold_bytes_per_launch(ev.n_stations, ev.n_dirs, ev.n_samples, 51) + extra * pairs
             row.update({"hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
                         "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 3)})
         res[name] = row

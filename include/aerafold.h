@@ -100,8 +100,8 @@ typedef struct ar_event {
                                   AERA antenna type's pattern resident at once), or NULL.
                                   Patterns may differ in grid. An id that was never loaded
                                   gives AR_STATUS_BAD_PATTERN and zero outputs for that
-                                  station's pairs. Stations grouped by pattern are fastest
-                                  (the interpolation is redone where the pattern changes). */
+                                  station's pairs. The unfold kernel walks each direction's
+                                  stations grouped by pattern, whatever their order here.  */
 } ar_event;
 
 /* Outputs, owned by the caller (DEVICE memory for ar_unfold, HOST memory for
@@ -124,6 +124,15 @@ typedef struct ar_outputs {
                                   1/2 (delta = 0 at the trace ends or without a strict
                                   maximum), in FP64 from the FP32 envelope. When given, the
                                   residual, t0 and chi2 use these times.                  */
+  float* snr;                  /* [D][S] or NULL. A variant the paper does not define: the
+                                  pulse's signal-to-noise ratio (peak_amp / noise)^2, noise^2
+                                  being the mean of envelope^2 over the samples more than N/16
+                                  from the peak (0 when there are none or that mean is 0), in
+                                  FP32. When given, the direction fit weights station s by
+                                  w_s = snr (timing variance taken inversely proportional to
+                                  the SNR): t0 = sum w (t - tau) / sum w, residual = t - tau -
+                                  t0, chi2 = sum w residual^2; unweighted if the weights sum
+                                  to 0.                                                   */
 } ar_outputs;
 
 /* Create a context on cfg->device (cfg may be NULL: device 0, defaults). The context owns

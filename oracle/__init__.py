@@ -61,6 +61,9 @@ def lib():
             L.orc_residual.argtypes = [I, P, P, D, D, D, P, P, P]
             L.orc_peak_offset.argtypes = [I, P, I]
             L.orc_peak_offset.restype = D
+            L.orc_snr.argtypes = [I, P, I]
+            L.orc_snr.restype = D
+            L.orc_residual_weighted.argtypes = [I, P, P, P, D, D, D, P, P, P]
             L.orc_unfold_event.argtypes = [PP, F, I, I, D, D, F, P, P, I, P,
                                            P, P, I32, P, P, P, P, P, U, P]
             L.orc_unfold_sample.argtypes = [PP, F, I, D, F, P, P, I, I32, I32,
@@ -167,6 +170,31 @@ def peak_offset(env: np.ndarray, k: int) -> float:
     """Sub-sample offset of the envelope maximum at sample k (parabola through k-1, k, k+1)."""
     e = np.ascontiguousarray(env, dtype=np.float64)
     return float(lib().orc_peak_offset(e.size, _p(e), int(k)))
+
+
+def snr(env: np.ndarray, k: int) -> float:
+    """(env[k] / noise)^2, noise^2 = mean of env^2 more than N/16 samples from k (0 if none)."""
+    e = np.ascontiguousarray(env, dtype=np.float64)
+    return float(lib().orc_snr(e.size, _p(e), int(k)))
+
+
+def event_snr(envelope: np.ndarray, peak_idx: np.ndarray) -> np.ndarray:
+    """SNR [D][S] of an event's envelopes [D][S][N] at the given peak indices [D][S]."""
+    D, S, _ = envelope.shape
+    return np.array([[snr(envelope[d, s], int(peak_idx[d, s])) for s in range(S)] for d in range(D)])
+
+
+def residual_weighted(pos: np.ndarray, peak_time: np.ndarray, w: np.ndarray, zen: float, az: float,
+                      n_refr: float = 1.0):
+    """Plane-wave residual with per-station weights (the unweighted fit when they sum to 0)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    pt = np.ascontiguousarray(peak_time, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    res = np.empty(pos.shape[0])
+    t0 = np.empty(1)
+    chi2 = np.empty(1)
+    lib().orc_residual_weighted(pos.shape[0], _p(pos), _p(pt), _p(ww), zen, az, n_refr, _p(res), _p(t0), _p(chi2))
+    return res, float(t0[0]), float(chi2[0])
 
 
 def fine_peak_times(envelope: np.ndarray, peak_idx: np.ndarray, t_start_ns: np.ndarray, fs_hz: float) -> np.ndarray:

@@ -269,6 +269,55 @@ double orc_peak_offset(int n, const double *env, int k) {
   return delta;
 }
 
+/* ---- signal-to-noise ratio and SNR-weighted residual (a variant: the paper defines no
+ * noise estimate and no timing weights) ---------------------------------------------------
+ * SNR of a pair: (env[k] / noise)^2 at the envelope maximum k, noise^2 being the mean of
+ * env[n]^2 over the samples with |n - k| > N/16 (the pulse is taken to lie within N/16
+ * samples of its maximum). 0 when no sample lies outside that window or their mean is 0. */
+double orc_snr(int n, const double *env, int k) {
+  int w = n / 16, count = 0;
+  double ss = 0.0;
+  for (int i = 0; i < n; ++i) {
+    int d = i > k ? i - k : k - i;
+    if (d > w) {
+      ss += env[i] * env[i];
+      count += 1;
+    }
+  }
+  if (count == 0 || !(ss > 0.0)) return 0.0;
+  double noise2 = ss / count;
+  return env[k] * env[k] / noise2;
+}
+
+/* Plane-wave residual with a weight w_s >= 0 per station (w = SNR: a station's timing
+ * variance taken inversely proportional to its SNR):
+ *   d_s = t_s - tau_s,  t0 = sum w d / sum w,  r_s = d_s - t0,  chi2 = sum w r^2.
+ * With sum w == 0 this is the unweighted fit (orc_residual). */
+void orc_residual_weighted(int n_st, const double *pos, const double *peak_time, const double *w,
+                           double zen, double az, double n_refr, double *res, double *t0, double *chi2) {
+  double sw = 0.0;
+  for (int s = 0; s < n_st; ++s) sw += w[s];
+  if (!(sw > 0.0)) {
+    orc_residual(n_st, pos, peak_time, zen, az, n_refr, res, t0, chi2);
+    return;
+  }
+  double nx = sin(zen) * cos(az), ny = sin(zen) * sin(az), nz = cos(zen);
+  double swd = 0.0;
+  for (int s = 0; s < n_st; ++s) {
+    double tau = -(nx * pos[3 * s] + ny * pos[3 * s + 1] + nz * pos[3 * s + 2]) * n_refr /
+                 ORC_C_M_PER_NS;
+    res[s] = peak_time[s] - tau;
+    swd += w[s] * res[s];
+  }
+  double mean = swd / sw, ss = 0.0;
+  for (int s = 0; s < n_st; ++s) {
+    res[s] = res[s] - mean;
+    ss += w[s] * res[s] * res[s];
+  }
+  *t0 = mean;
+  *chi2 = ss;
+}
+
 /* ---- whole event -------------------------------------------------------------------- */
 
 /* All pairs of one event. Output layouts: efield [D][S][2][N], env [D][S][N],

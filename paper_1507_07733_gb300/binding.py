@@ -75,7 +75,7 @@ class ar_outputs(ctypes.Structure):
     _fields_ = [("efield", ctypes.c_void_p), ("envelope", ctypes.c_void_p), ("peak_idx", ctypes.c_void_p),
                 ("peak_amp", ctypes.c_void_p), ("peak_time_ns", ctypes.c_void_p),
                 ("residual_ns", ctypes.c_void_p), ("t0_ns", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
-                ("status", ctypes.c_void_p), ("peak_time_fine_ns", ctypes.c_void_p)]
+                ("status", ctypes.c_void_p), ("peak_time_fine_ns", ctypes.c_void_p), ("snr", ctypes.c_void_p)]
 
 
 class ar_recon_out(ctypes.Structure):
@@ -309,10 +309,11 @@ def make_event(pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: floa
 
 
 def alloc_outputs(n_dirs: int, n_stations: int, n_samples: int, device="cuda", traces: bool = True,
-                  pin_memory: bool = False, fine: bool = False):
+                  pin_memory: bool = False, fine: bool = False, snr: bool = False):
     """Allocate output tensors with the library's layouts; returns (dict, ar_outputs). With
     ``fine`` the dict also holds ``peak_time_fine_ns`` (sub-sample peak times; the residual
-    then uses them)."""
+    then uses them); with ``snr`` it holds ``snr`` (pulse SNRs; the residual then weights
+    stations by them)."""
     import torch
     D, S, N = n_dirs, n_stations, n_samples
     kw = dict(device=device)
@@ -331,12 +332,15 @@ def alloc_outputs(n_dirs: int, n_stations: int, n_samples: int, device="cuda", t
     )
     if fine:
         o["peak_time_fine_ns"] = torch.empty((D, S), dtype=torch.float64, **kw)
+    if snr:
+        o["snr"] = torch.empty((D, S), dtype=torch.float32, **kw)
     return o, outputs_struct(o)
 
 
 def outputs_struct(o: dict) -> ar_outputs:
     return ar_outputs(*[_ptr(o.get(k)) for k in ("efield", "envelope", "peak_idx", "peak_amp", "peak_time_ns",
-                                                  "residual_ns", "t0_ns", "chi2", "status", "peak_time_fine_ns")])
+                                                  "residual_ns", "t0_ns", "chi2", "status", "peak_time_fine_ns",
+                                                  "snr")])
 
 
 class Context:

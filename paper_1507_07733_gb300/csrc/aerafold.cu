@@ -412,6 +412,7 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.peak_amp = out->peak_amp;
   d.peak_time = out->peak_time_ns;
   d.peak_fine = out->peak_time_fine_ns;
+  d.snr = out->snr;
   d.status = out->status;
   d.residual = out->residual_ns;
   d.t0 = out->t0_ns;
@@ -771,16 +772,17 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
     return fail(ctx, AR_ERR_UNSUPPORTED_N, "n_samples=%zu: supported lengths are 1024, 2048, 4096", N);
   // staging slots: 0 traces, 1 pos, 2 t_start, 3 dirs, 4 efield, 5 envelope, 6 peak_idx,
   // 7 peak_amp, 8 peak_time, 9 residual, 10 t0, 11 chi2, 12 status, 13 station patterns,
-  // 14 fine peak times
-  const size_t sizes[15] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
+  // 14 fine peak times, 15 SNRs
+  const size_t sizes[16] = {S * 2 * N * sizeof(float), S * 3 * sizeof(double), S * sizeof(double),
                             D * 2 * sizeof(double), out->efield ? D * S * 2 * N * sizeof(float) : 0,
                             out->envelope ? D * S * N * sizeof(float) : 0, D * S * sizeof(int32_t),
                             D * S * sizeof(float), D * S * sizeof(double), D * S * sizeof(double),
                             D * sizeof(double), D * sizeof(double), D * S * sizeof(uint32_t),
                             ev->station_pattern ? S * sizeof(int32_t) : 0,
-                            out->peak_time_fine_ns ? D * S * sizeof(double) : 0};
-  if (ctx->stage.size() < 15) ctx->stage.resize(15, {nullptr, 0});
-  for (int i = 0; i < 15; ++i) {
+                            out->peak_time_fine_ns ? D * S * sizeof(double) : 0,
+                            out->snr ? D * S * sizeof(float) : 0};
+  if (ctx->stage.size() < 16) ctx->stage.resize(16, {nullptr, 0});
+  for (int i = 0; i < 16; ++i) {
     if (sizes[i] > ctx->stage[i].second) {
       AR_CUDA(ctx, cudaDeviceSynchronize());
       cudaFree(ctx->stage[i].first);
@@ -814,11 +816,12 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   dout.chi2 = static_cast<double*>(dev(11));
   dout.status = static_cast<uint32_t*>(dev(12));
   dout.peak_time_fine_ns = out->peak_time_fine_ns ? static_cast<double*>(dev(14)) : nullptr;
+  dout.snr = out->snr ? static_cast<float*>(dev(15)) : nullptr;
   if ((st = ar_unfold(ctx, &de, &dout, stream)) != AR_OK) return st;
-  void* hosts[15] = {nullptr, nullptr, nullptr, nullptr, out->efield, out->envelope, out->peak_idx,
+  void* hosts[16] = {nullptr, nullptr, nullptr, nullptr, out->efield, out->envelope, out->peak_idx,
                      out->peak_amp, out->peak_time_ns, out->residual_ns, out->t0_ns, out->chi2, out->status,
-                     nullptr, out->peak_time_fine_ns};
-  for (int i = 4; i < 15; ++i)
+                     nullptr, out->peak_time_fine_ns, out->snr};
+  for (int i = 4; i < 16; ++i)
     if (hosts[i] && sizes[i]) AR_CUDA(ctx, cudaMemcpyAsync(hosts[i], dev(i), sizes[i], cudaMemcpyDeviceToHost, s));
   return ar_sync(ctx, stream);
 }
@@ -1496,6 +1499,7 @@ size_t req_state_bytes(const ar_event& ev, const ar_outputs& out) {
   if (out.envelope) b += r(D * S * N * 4);
   b += r(D * S * 4) * 2 + r(D * S * 8) * 2 + r(D * 8) * 2 + r(D * S * 4);
   if (out.peak_time_fine_ns) b += r(D * S * 8);
+  if (out.snr) b += r(D * S * 4);
   return b;
 }
 
@@ -1547,6 +1551,7 @@ void place_request(ar_server* sv, Request& r) {
   r.dev_out.chi2 = reinterpret_cast<double*>(take(D * 8));
   r.dev_out.status = reinterpret_cast<uint32_t*>(take(D * S * 4));
   if (r.out.peak_time_fine_ns) r.dev_out.peak_time_fine_ns = reinterpret_cast<double*>(take(D * S * 8));
+  if (r.out.snr) r.dev_out.snr = reinterpret_cast<float*>(take(D * S * 4));
 }
 
 cudaError_t copy_in(ar_server* sv, const Request& r) {
@@ -1579,7 +1584,8 @@ cudaError_t copy_out(ar_server* sv, const Request& r) {
                         {r.out.t0_ns, r.dev_out.t0_ns, D * 8},
                         {r.out.chi2, r.dev_out.chi2, D * 8},
                         {r.out.status, r.dev_out.status, D * S * 4},
-                        {r.out.peak_time_fine_ns, r.dev_out.peak_time_fine_ns, D * S * 8}};
+                        {r.out.peak_time_fine_ns, r.dev_out.peak_time_fine_ns, D * S * 8},
+                        {r.out.snr, r.dev_out.snr, D * S * 4}};
   for (const Item& it : items) {
     if (!it.h || !it.d) continue;
     cudaError_t e = cudaMemcpyAsync(it.h, it.d, it.n, cudaMemcpyDeviceToHost, sv->s_d2h);

@@ -176,6 +176,7 @@ struct EventDesc {
   float* peak_amp;         // [D][S]
   double* peak_time;       // [D][S]
   double* peak_fine;       // [D][S] sub-sample peak times, or null (then the residual uses peak_time)
+  float* snr;              // [D][S] pulse SNR, or null; when given the residual weights stations by it
   unsigned* status;        // [D][S]
   double* residual;        // [D][S]
   double* t0;              // [D]
@@ -502,8 +503,8 @@ struct UnfoldSmem {
   static constexpr size_t HINV = A + sizeof(float2) * L::A_F2;
   static constexpr size_t EV = HINV + 2 * sizeof(float4) * L::M;            // current EventDesc
   static constexpr size_t DIR = EV + ((sizeof(EventDesc) + 15) / 16) * 16;  // 1 DirInfo
-  static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // T/32 x (double, float, int) + flags
-  static constexpr size_t BAR = RED + 16 * (L::T / 32) + 32;
+  static constexpr size_t RED = DIR + ((sizeof(DirInfo) + 15) / 16) * 16;   // reductions
+  static constexpr size_t BAR = RED + 20 * (L::T / 32) + 32;   // T/32 x (double, float, int, float) + flag
   static constexpr size_t SLAB = BAR + 16;   // 4 * n_f * 4 float2 (staged corner slabs)
   // the per-node values and slopes (8 float2 per node) are formed in A before the solve
   static_assert(sizeof(float2) * L::A_F2 >= sizeof(float2) * 8 * kMaxFreqNodes, "node scratch must fit in A");
@@ -521,6 +522,34 @@ __device__ __forceinline__ double peak_offset(const float* env, int n, int k) {
   if (!(second < 0.0)) return 0.0;
   const double delta = __ddiv_rn(__dmul_rn(0.5, __dsub_rn(a, c)), second);
   return fmin(0.5, fmax(-0.5, delta));
+}
+
+// Pulse SNR of a pair (a variant; the paper defines no noise estimate): (peak / noise)^2 at
+// the envelope maximum k, noise^2 the mean of env^2 over the samples more than n/16 from k;
+// 0 when there are none or their mean is 0. Whole CTA over the envelope in shared memory:
+// thread t sums samples t, t + T, ..., the warps combine in a fixed tree and thread 0 adds the
+// warps in order; the result is thread 0's. red holds T/32 floats.
+template <int T>
+__device__ __forceinline__ float pair_snr(const float* env, int n, int k, float peak, float* red) {
+  const int w = n / 16;
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += T) {
+    const int dd = i > k ? i - k : k - i;
+    if (dd > w) acc = fmaf(env[i], env[i], acc);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  float snr = 0.f;
+  if (threadIdx.x == 0) {
+    float ss = red[0];
+#pragma unroll
+    for (int i = 1; i < T / 32; ++i) ss += red[i];
+    const int count = n - (min(k + w, n - 1) - max(k - w, 0) + 1);
+    if (count > 0 && ss > 0.f) snr = peak * peak / (ss / static_cast<float>(count));
+  }
+  return snr;
 }
 
 // Residual of direction d over all stations, by the whole CTA (FP64, deterministic order:
@@ -556,13 +585,30 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   __syncthreads();
   const double nx = red[0], ny = red[1], nz = red[2];
   const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
-  double acc = 0.0;
+  // with SNRs the fit weights station s by w_s = snr (a variant; its timing variance taken
+  // inversely proportional to the SNR): t0 = sum w d / sum w, chi2 = sum w r^2; unweighted
+  // when there are none or they sum to 0
+  const float* wp = p.snr ? p.snr + static_cast<size_t>(d) * p.n_st : nullptr;
+  double acc = 0.0, accw = 0.0, accwd = 0.0;
   for (int s = threadIdx.x; s < p.n_st; s += T) {
     const double* x = p.pos + 3 * s;
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    acc = __dadd_rn(acc, __dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c)));   // t_s - tau_s
+    const double ds = __dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c));   // t_s - tau_s
+    acc = __dadd_rn(acc, ds);
+    if (wp) {
+      const double w = static_cast<double>(__ldcg(wp + s));
+      accw = __dadd_rn(accw, w);
+      accwd = __dadd_rn(accwd, __dmul_rn(w, ds));
+    }
   }
-  const double mean = __ddiv_rn(block_sum_fixed<T>(acc, red), static_cast<double>(p.n_st));
+  const double sum = block_sum_fixed<T>(acc, red);
+  double sw = 0.0, swd = 0.0;
+  if (wp) {
+    sw = block_sum_fixed<T>(accw, red);
+    swd = block_sum_fixed<T>(accwd, red);
+  }
+  const bool weighted = wp && sw > 0.0;
+  const double mean = weighted ? __ddiv_rn(swd, sw) : __ddiv_rn(sum, static_cast<double>(p.n_st));
   double ss = 0.0;
   double* res = p.residual + static_cast<size_t>(d) * p.n_st;
   for (int s = threadIdx.x; s < p.n_st; s += T) {
@@ -570,7 +616,7 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
     const double r = __dsub_rn(__dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c)), mean);
     res[s] = r;
-    ss = __fma_rn(r, r, ss);
+    ss = weighted ? __fma_rn(__dmul_rn(static_cast<double>(__ldcg(wp + s)), r), r, ss) : __fma_rn(r, r, ss);
   }
   ss = block_sum_fixed<T>(ss, red);
   if (threadIdx.x == 0) {
@@ -717,6 +763,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
   float* redv = reinterpret_cast<float*>(redd + T / 32);             // T/32 floats
   int* redi = reinterpret_cast<int*>(redv + T / 32);                 // T/32 ints
   int* sflag = redi + T / 32;                                        // 1 int
+  float* redw = reinterpret_cast<float*>(sflag + 1);                // T/32 floats (SNR noise sums)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + SM::BAR);
   float2* slab = reinterpret_cast<float2*>(smem_raw + SM::SLAB);
 
@@ -884,7 +931,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     // exchange uses the first 16M bytes (where E was).
     const size_t pair = static_cast<size_t>(d) * S + s;
     const bool traces = ev.efield != nullptr;
-    const bool stage_env = traces || ev.peak_fine != nullptr;   // the sub-sample peak reads the envelope
+    const bool stage_env = traces || ev.peak_fine != nullptr || ev.snr != nullptr;   // read back by those
     float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(A) + 16 * M);
     float bv = -1.0f;
     int bi = 0;
@@ -965,6 +1012,17 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       if (ev.envelope) tma_bulk_s2g(ev.envelope + pair * N, stage + 2 * N, N * sizeof(float));
       tma_bulk_commit();
     }
+    float snr = 0.f;
+    if (ev.snr) {   // every thread takes the pair's peak from the per-warp maxima (as thread 0 does below)
+      float pv = redv[0];
+      int pk = redi[0];
+#pragma unroll
+      for (int w = 1; w < T / 32; ++w) {
+        if (redv[w] > pv || (redv[w] == pv && redi[w] < pk)) { pv = redv[w]; pk = redi[w]; }
+      }
+      if (pv < 0.f) { pv = 0.f; pk = 0; }
+      snr = pair_snr<T>(stage + 2 * N, N, pk, pv, redw);
+    }
     if (tid == 0) {
 #pragma unroll
       for (int w = 1; w < T / 32; ++w) {
@@ -979,6 +1037,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
             __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(stage + 2 * N, N, bi)),
                                                ev.dt_ns));
       ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
+      if (ev.snr) ev.snr[pair] = snr;
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
         __threadfence();
         const unsigned before = atomicAdd(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));

@@ -503,16 +503,26 @@ __global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_cons
   }
   if ((n2 & 31) == 0) { rv[n2 >> 5] = bv; ri[n2 >> 5] = bi; }
   __syncthreads();
+  __shared__ float pk_v;
+  __shared__ int pk_i;
   if (n2 == 0) {
     for (int w = 1; w < kSub / 32; ++w)
       if (rv[w] > bv || (rv[w] == bv && ri[w] < bi)) { bv = rv[w]; bi = ri[w]; }
     if (bv < 0.f) { bv = 0.f; bi = 0; }
+    pk_v = bv;
+    pk_i = bi;
     ev.peak_idx[pair] = bi;
     ev.peak_amp[pair] = bv;
     ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
     if (ev.peak_fine)
       ev.peak_fine[pair] =
           __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(senv, N, bi)), ev.dt_ns));
+  }
+  if (ev.snr) {
+    __shared__ float rw[kSub / 32];
+    __syncthreads();   // the pair's peak visible to every thread
+    const float snr = pair_snr<kSub>(senv, N, pk_i, pk_v, rw);
+    if (n2 == 0) ev.snr[pair] = snr;
   }
 }
 
