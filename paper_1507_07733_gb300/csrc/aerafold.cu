@@ -303,6 +303,17 @@ ar_status ensure_spec(ar_ctx* ctx, size_t bytes) {
   return AR_OK;
 }
 
+// the dynamic shared-memory limit of both unfold instantiations of a length
+template <int N_>
+cudaError_t set_unfold_smem_limit(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(unfold_kernel<N_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(bytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(unfold_kernel<N_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(bytes));
+  return e;
+}
+
 template <int N_>
 ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);
@@ -312,13 +323,12 @@ ar_status unfold_cfg(ar_ctx* ctx, int n_f, KernelCfg** out) {
     KernelCfg kc;
     // the attribute belongs to the kernel, not to this configuration: set it to the largest
     // layout any pattern can need, so that no later set-up lowers it below a cached launch
-    AR_CUDA(ctx, cudaFuncSetAttribute(unfold_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(UnfoldSmem<N_>::total(kMaxFreqNodes))));
+    AR_CUDA(ctx, set_unfold_smem_limit<N_>(UnfoldSmem<N_>::total(kMaxFreqNodes)));
     // stage the corner slabs by TMA unless that lowers the CTAs per SM (large patterns)
     int per_sm = 0, per_sm_direct = 0;
-    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, Layout<N_>::T,
+    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_, false>, Layout<N_>::T,
                                                                UnfoldSmem<N_>::total(n_f)));
-    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_>, Layout<N_>::T,
+    AR_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_, false>, Layout<N_>::T,
                                                                UnfoldSmem<N_>::total(n_f, true)));
     kc.slab_direct = per_sm_direct > per_sm ? 1 : 0;
     if (kc.slab_direct) per_sm = per_sm_direct;
@@ -463,8 +473,10 @@ cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cuda
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
   const long long pairs = static_cast<long long>(desc.n_st) * desc.n_dir;
   const long long grid = std::min<long long>(grid_cap, pairs);
-  if ((e = launch_pdl(unfold_kernel<N_>, static_cast<int>(grid), L::T,
-                      UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0), stream, pp)) != cudaSuccess)
+  const size_t smem = UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0);
+  if ((e = desc.snr ? launch_pdl(unfold_kernel<N_, true>, static_cast<int>(grid), L::T, smem, stream, pp)
+                    : launch_pdl(unfold_kernel<N_, false>, static_cast<int>(grid), L::T, smem, stream, pp)) !=
+      cudaSuccess)
     return e;
   if (evs && (e = cudaEventRecord(evs[2], stream)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -685,9 +697,10 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
   plane_fit_kernel<<<1, 128, 0, stream>>>(fp);
   for (int it = 1; it <= max_iter; ++it) {
-    if ((e = launch_pdl(unfold_kernel<N_>, std::min(rs.kc->grid, S), L::T,
-                        UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0),
-                        stream, pp)) != cudaSuccess)
+    const size_t smem = UnfoldSmem<N_>::total(pp.ev0.n_f_layout, pp.ev0.slab_direct != 0);
+    if ((e = pp.ev0.snr ? launch_pdl(unfold_kernel<N_, true>, std::min(rs.kc->grid, S), L::T, smem, stream, pp)
+                        : launch_pdl(unfold_kernel<N_, false>, std::min(rs.kc->grid, S), L::T, smem, stream, pp)) !=
+        cudaSuccess)
       return e;
     fp.times = out->last.peak_time_ns;
     fp.idx = out->last.peak_idx;
@@ -1115,7 +1128,7 @@ struct ar_batch {
   float4* spec = nullptr;                      // station spectra of all events
   size_t spec_bytes = 0;
   unsigned* dir_done = nullptr;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2][2] = {};            // [staging set][with SNRs], built when first needed
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool pending[2] = {false, false};
   int next = 0;
@@ -1150,15 +1163,17 @@ cudaError_t batch_station_launch(ar_batch* b, int c, cudaStream_t st) {
 // The first unfold kernel waits for the last station kernel (so for all of them); the later
 // ones need not wait: the kernel before them launches its dependents only after its own wait.
 template <int N_>
-cudaError_t batch_unfold_launch(ar_batch* b, int c, int ctas_per_sm, int wait_prior, cudaStream_t st) {
+cudaError_t batch_unfold_launch(ar_batch* b, int c, int ctas_per_sm, int wait_prior, bool snr, cudaStream_t st) {
   using L = Layout<N_>;
-  return launch_pdl(unfold_kernel<N_>, ctas_per_sm * b->ctx->num_sms, L::T,
-                    UnfoldSmem<N_>::total(b->lim.max_n_freq, b->slab_direct[c] != 0), st,
-                    batch_params<N_>(b, c, wait_prior));
+  const int grid = ctas_per_sm * b->ctx->num_sms;
+  const size_t smem = UnfoldSmem<N_>::total(b->lim.max_n_freq, b->slab_direct[c] != 0);
+  return snr ? launch_pdl(unfold_kernel<N_, true>, grid, L::T, smem, st, batch_params<N_>(b, c, wait_prior))
+             : launch_pdl(unfold_kernel<N_, false>, grid, L::T, smem, st, batch_params<N_>(b, c, wait_prior));
 }
 
-// capture the whole launch (descriptor copies, then per class the two kernels) into graph g
-ar_status batch_build_graph(ar_batch* b, int set, const int* ctas, cudaGraphExec_t* out) {
+// capture the whole launch (descriptor copies, then per class the two kernels) into graph g;
+// snr: with the unfold instantiation that computes pulse SNRs
+ar_status batch_build_graph(ar_batch* b, int set, const int* ctas, bool snr, cudaGraphExec_t* out) {
   ar_ctx* ctx = b->ctx;
   cudaStream_t cs;
   AR_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1171,9 +1186,9 @@ ar_status batch_build_graph(ar_batch* b, int set, const int* ctas, cudaGraphExec
   if (e == cudaSuccess) e = batch_station_launch<1024>(b, 0, cs);
   if (e == cudaSuccess) e = batch_station_launch<2048>(b, 1, cs);
   if (e == cudaSuccess) e = batch_station_launch<4096>(b, 2, cs);
-  if (e == cudaSuccess) e = batch_unfold_launch<4096>(b, 2, ctas[2], 1, cs);
-  if (e == cudaSuccess) e = batch_unfold_launch<2048>(b, 1, ctas[1], 0, cs);
-  if (e == cudaSuccess) e = batch_unfold_launch<1024>(b, 0, ctas[0], 0, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<4096>(b, 2, ctas[2], 1, snr, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<2048>(b, 1, ctas[1], 0, snr, cs);
+  if (e == cudaSuccess) e = batch_unfold_launch<1024>(b, 0, ctas[0], 0, snr, cs);
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
@@ -1267,9 +1282,9 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
   if (e != cudaSuccess) return cleanup(fail(ctx, AR_ERR_OUT_OF_MEMORY, "batch allocation failed: %s", cudaGetErrorString(e)));
   for (int c = 0; c < kClasses; ++c) {
     for (int set = 0; set < 2; ++set) std::memset(b->h_stage[set][c], 0, b->desc_bytes);
-    const void* fn = c == 0 ? reinterpret_cast<const void*>(unfold_kernel<1024>)
-                     : c == 1 ? reinterpret_cast<const void*>(unfold_kernel<2048>)
-                              : reinterpret_cast<const void*>(unfold_kernel<4096>);
+    const void* fn = c == 0 ? reinterpret_cast<const void*>(unfold_kernel<1024, false>)
+                     : c == 1 ? reinterpret_cast<const void*>(unfold_kernel<2048, false>)
+                              : reinterpret_cast<const void*>(unfold_kernel<4096, false>);
     const int threads = c == 0 ? Layout<1024>::T : c == 1 ? Layout<2048>::T : Layout<4096>::T;
     const auto smem_of = [&](bool direct) {
       return c == 0 ? UnfoldSmem<1024>::total(lim->max_n_freq, direct)
@@ -1283,8 +1298,9 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
     const size_t smem_max = c == 0 ? UnfoldSmem<1024>::total(kMaxFreqNodes)
                             : c == 1 ? UnfoldSmem<2048>::total(kMaxFreqNodes)
                                      : UnfoldSmem<4096>::total(kMaxFreqNodes);
-    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max))) !=
-            cudaSuccess ||
+    if ((e = c == 0   ? set_unfold_smem_limit<1024>(smem_max)
+             : c == 1 ? set_unfold_smem_limit<2048>(smem_max)
+                      : set_unfold_smem_limit<4096>(smem_max)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(sfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp_smem))) != cudaSuccess ||
         (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas_per_sm[c], fn, threads, smem_of(false))) !=
             cudaSuccess)
@@ -1300,7 +1316,7 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
     b->ctas_per_sm[c] = b->max_ctas_per_sm[c];
   }
   for (int set = 0; set < 2; ++set) {
-    ar_status st = batch_build_graph(b, set, b->ctas_per_sm, &b->exec[set]);
+    ar_status st = batch_build_graph(b, set, b->ctas_per_sm, false, &b->exec[set][0]);
     if (st != AR_OK) return cleanup(st);
   }
   b->tuned = !ctx->cfg.autotune;
@@ -1313,7 +1329,8 @@ ar_status ar_batch_destroy(ar_batch* b) {
   cudaSetDevice(b->ctx->device);
   for (int set = 0; set < 2; ++set) {
     if (b->pending[set]) cudaEventSynchronize(b->done[set]);
-    if (b->exec[set]) cudaGraphExecDestroy(b->exec[set]);
+    for (int v = 0; v < 2; ++v)
+      if (b->exec[set][v]) cudaGraphExecDestroy(b->exec[set][v]);
     if (b->done[set]) cudaEventDestroy(b->done[set]);
   }
   for (int c = 0; c < kClasses; ++c) {
@@ -1328,7 +1345,7 @@ ar_status ar_batch_destroy(ar_batch* b) {
 
 // Autotune: time the whole graph for each unfold occupancy 1..max CTAs per SM (clamped per
 // class) on the current staging set, keep the fastest, rebuild both graphs with it.
-static ar_status batch_autotune(ar_batch* b, int set, cudaStream_t stream) {
+static ar_status batch_autotune(ar_batch* b, int set, bool snr, cudaStream_t stream) {
   ar_ctx* ctx = b->ctx;
   int best_k = 0;
   float best_ms = 0.f;
@@ -1340,7 +1357,7 @@ static ar_status batch_autotune(ar_batch* b, int set, cudaStream_t stream) {
     int ctas[kClasses];
     for (int c = 0; c < kClasses; ++c) ctas[c] = std::min(k, b->max_ctas_per_sm[c]);
     cudaGraphExec_t g = nullptr;
-    ar_status st = batch_build_graph(b, set, ctas, &g);
+    ar_status st = batch_build_graph(b, set, ctas, snr, &g);
     if (st != AR_OK) return st;
     float ms_sum = 0.f;
     for (int rep = 0; rep < 4; ++rep) {
@@ -1365,9 +1382,11 @@ static ar_status batch_autotune(ar_batch* b, int set, cudaStream_t stream) {
   for (int s2 = 0; s2 < 2; ++s2) {
     if (b->pending[s2]) AR_CUDA(ctx, cudaEventSynchronize(b->done[s2]));
     b->pending[s2] = false;
-    cudaGraphExecDestroy(b->exec[s2]);
-    b->exec[s2] = nullptr;
-    ar_status st = batch_build_graph(b, s2, b->ctas_per_sm, &b->exec[s2]);
+    for (int v = 0; v < 2; ++v) {
+      if (b->exec[s2][v]) cudaGraphExecDestroy(b->exec[s2][v]);
+      b->exec[s2][v] = nullptr;
+    }
+    ar_status st = batch_build_graph(b, s2, b->ctas_per_sm, snr, &b->exec[s2][snr ? 1 : 0]);
     if (st != AR_OK) return st;
   }
   b->tuned = true;
@@ -1388,10 +1407,14 @@ ar_status ar_batch_run(ar_batch* b, const ar_event* events, const ar_outputs* ou
   b->pending[set] = false;
   ar_status st = batch_fill(b, set, events, outs, n_events);
   if (st != AR_OK) return st;
+  bool snr = false;
+  for (int i = 0; i < n_events; ++i) snr = snr || outs[i].snr != nullptr;
   if (!b->tuned) {
-    if ((st = batch_autotune(b, set, s)) != AR_OK) return st;
+    if ((st = batch_autotune(b, set, snr, s)) != AR_OK) return st;
   }
-  AR_CUDA(ctx, cudaGraphLaunch(b->exec[set], s));
+  cudaGraphExec_t& g = b->exec[set][snr ? 1 : 0];
+  if (!g && (st = batch_build_graph(b, set, b->ctas_per_sm, snr, &g)) != AR_OK) return st;
+  AR_CUDA(ctx, cudaGraphLaunch(g, s));
   AR_CUDA(ctx, cudaEventRecord(b->done[set], s));
   b->pending[set] = true;
   b->next = set ^ 1;
@@ -1940,9 +1963,9 @@ ar_status noalloc_setup(int dev, NoAllocDevice** out) {
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp1)));
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp2)));
     AR_NA_CUDA(cudaFuncSetAttribute(station_spectrum_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sp4)));
-    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<1024>::total(kMaxFreqNodes))));
-    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<2048>::total(kMaxFreqNodes))));
-    AR_NA_CUDA(cudaFuncSetAttribute(unfold_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(UnfoldSmem<4096>::total(kMaxFreqNodes))));
+    AR_NA_CUDA(set_unfold_smem_limit<1024>(UnfoldSmem<1024>::total(kMaxFreqNodes)));
+    AR_NA_CUDA(set_unfold_smem_limit<2048>(UnfoldSmem<2048>::total(kMaxFreqNodes)));
+    AR_NA_CUDA(set_unfold_smem_limit<4096>(UnfoldSmem<4096>::total(kMaxFreqNodes)));
     d.scratch = static_cast<unsigned char*>(p);
     d.ready = true;
   }
@@ -1972,9 +1995,9 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
                                                      pd->n_freq);
   AR_NA_CUDA(cudaGetLastError());
   int per_sm = 0, per_sm_direct = 0;
-  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_>, L::T,
+  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unfold_kernel<N_, false>, L::T,
                                                            UnfoldSmem<N_>::total(pd->n_freq)));
-  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_>, L::T,
+  AR_NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, unfold_kernel<N_, false>, L::T,
                                                            UnfoldSmem<N_>::total(pd->n_freq, true)));
   EventDesc desc = make_desc(b, *pd, reinterpret_cast<const float2*>(table), ev, out, k_lo);
   if (per_sm_direct > per_sm) {   // corner slabs read from L2 where staging them costs occupancy

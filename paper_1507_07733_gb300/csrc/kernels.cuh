@@ -745,7 +745,9 @@ __device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const 
   return __syncthreads_or(sing);
 }
 
-template <int N_>
+// kSnr: the instantiation that can compute pulse SNRs (for events that request them); the
+// other one carries none of that code, which costs the plain path time even when unused.
+template <int N_, bool kSnr>
 __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_kernel(const __grid_constant__ PathParams prm) {
   using L = Layout<N_>;
   using SM = UnfoldSmem<N_>;
@@ -931,7 +933,8 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     // exchange uses the first 16M bytes (where E was).
     const size_t pair = static_cast<size_t>(d) * S + s;
     const bool traces = ev.efield != nullptr;
-    const bool stage_env = traces || ev.peak_fine != nullptr || ev.snr != nullptr;   // read back by those
+    const bool want_snr = kSnr && ev.snr != nullptr;
+    const bool stage_env = traces || ev.peak_fine != nullptr || want_snr;   // read back by those
     float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(A) + 16 * M);
     float bv = -1.0f;
     int bi = 0;
@@ -1013,7 +1016,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       tma_bulk_commit();
     }
     float snr = 0.f;
-    if (ev.snr) {   // every thread takes the pair's peak from the per-warp maxima (as thread 0 does below)
+    if (want_snr) {   // every thread takes the pair's peak from the per-warp maxima (as thread 0 does below)
       float pv = redv[0];
       int pk = redi[0];
 #pragma unroll
@@ -1037,7 +1040,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
             __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(stage + 2 * N, N, bi)),
                                                ev.dt_ns));
       ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
-      if (ev.snr) ev.snr[pair] = snr;
+      if (want_snr) ev.snr[pair] = snr;
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
         __threadfence();
         const unsigned before = atomicAdd(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
