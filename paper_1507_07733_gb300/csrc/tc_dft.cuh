@@ -181,9 +181,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   const int cpg = p.chunks_per_group;
   const int nk = my_items * cpg;
   const int planes = p.terms == 6 ? 3 : 2;
-  // Chunks per fold: 2 when an item's chunk count is even (K = 128 accumulated on the tensor
-  // cores between folds), else 1.
-  const int F = cpg % 2 == 0 ? 2 : 1;
+  // Chunks per fold: up to 4 (K = 256 accumulated on the tensor cores between folds), a
+  // divisor of the item's chunk count; an item of at most 4 chunks is one fold unit, whose
+  // fold only moves the accumulator to global memory.
+  const int F = cpg <= 4 ? cpg : cpg % 4 == 0 ? 4 : cpg % 2 == 0 ? 2 : 1;
   const int nu = nk / F;   // fold units
 
   if (warp == 0) {
