@@ -50,10 +50,11 @@ constexpr int kBandPhase = 128;                   // band bins per sub-block pha
 constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile and K chunk
 constexpr unsigned kBlk = kBM * kBK * 2;          // bytes of one BF16 plane of a 128 x 64 block (16 KB)
 constexpr unsigned kStageBytes = 6 * kBlk;        // A and B, up to 3 planes each
-constexpr int kStages = 2;
+constexpr int kStages = 2;                          // ring bytes: 2 such stages (x6) or 3 of 4 blocks (x3)
 constexpr int kFwdK = 2 * kSub, kFwdN = 2 * kBandPhase;   // forward GEMM: K 1024, 256 outputs
 constexpr int kInvK = 2 * kBandPhase, kInvN = 2 * kSub;   // inverse GEMM: K 256, 1024 outputs
-constexpr size_t kGemmSmem = kStages * kStageBytes + 256;
+constexpr size_t kEpiBytes = 4 * 32 * 32 * sizeof(float);   // a 32 x 32 transpose tile per fold warp
+constexpr size_t kGemmSmem = kStages * kStageBytes + 256 + kEpiBytes;
 constexpr int kGemmThreads = 192;
 
 // byte offset of element (r, c) inside a 128-row, 64-column K-major BF16 block
@@ -166,12 +167,12 @@ constexpr int kTmemCols = 512;   // S, P0, P1: 128 columns each, rounded up to a
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  uint64_t* full = bars;          // [2] stage filled (bulk copies complete)
-  uint64_t* empty = bars + 2;     // [2] stage consumed (its MMAs complete)
-  uint64_t* ready = bars + 4;     // [2] partial region holds a finished chunk
-  uint64_t* pfree = bars + 6;     // [2] partial region folded (4 arrivals, one per fold warp)
-  uint64_t* done = bars + 8;      // every MMA complete
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 9);
+  uint64_t* full = bars;          // [3] stage filled (bulk copies complete)
+  uint64_t* empty = bars + 3;     // [3] stage consumed (its MMAs complete)
+  uint64_t* ready = bars + 6;     // [2] partial region holds a finished chunk
+  uint64_t* pfree = bars + 8;     // [2] partial region folded (4 arrivals, one per fold warp)
+  uint64_t* done = bars + 10;     // every MMA complete
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 11);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int items = p.m_tiles * p.n_tiles * p.groups;
   // Persistent: this CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; their chunks
@@ -181,6 +182,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   const int cpg = p.chunks_per_group;
   const int nk = my_items * cpg;
   const int planes = p.terms == 6 ? 3 : 2;
+  // The stage ring: two stages of 3 + 3 planes, or three of 2 + 2 planes, in the same bytes.
+  const int nst = planes == 2 ? 3 : 2;
+  const unsigned stage_bytes = 2u * planes * kBlk;
   // Chunks per fold: up to 4 (K = 256 accumulated on the tensor cores between folds), a
   // divisor of the item's chunk count; an item of at most 4 chunks is one fold unit, whose
   // fold only moves the accumulator to global memory.
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int i = 0; i < 9; ++i) mbar_init(bars + i, (i == 6 || i == 7) ? 4 : 1);
+    for (int i = 0; i < 11; ++i) mbar_init(bars + i, (i == 8 || i == 9) ? 4 : 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -207,45 +211,45 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
     if (lane == 0) {
       int issued = 0;
       for (int i = 0; i < nk && ok; ++i) {
-        const int s = i & 1;
-        if (i >= 2) ok = mbar_wait_bounded(&empty[s], ((i >> 1) - 1) & 1, kWaitLimitNs);
+        const int s = i % nst;
+        if (i >= nst) ok = mbar_wait_bounded(&empty[s], (i / nst - 1) & 1, kWaitLimitNs);
         if (!ok) break;
         const GemmItem w = gemm_item(p, i / cpg);
         const int kc = w.g * cpg + i % cpg;
-        unsigned char* st = smem + s * kStageBytes;
+        unsigned char* st = smem + s * stage_bytes;
         mbar_arrive_expect_tx(&full[s], 2u * planes * kBlk);
         for (int pl = 0; pl < planes; ++pl) {
           tma_bulk_g2s(st + pl * kBlk, p.a[pl] + (static_cast<size_t>(w.mt) * p.chunks + kc) * (kBlk / 16), kBlk,
                        &full[s]);
-          tma_bulk_g2s(st + (3 + pl) * kBlk, p.b[pl] + (static_cast<size_t>(w.nt) * p.chunks + kc) * (kBlk / 16),
+          tma_bulk_g2s(st + (planes + pl) * kBlk, p.b[pl] + (static_cast<size_t>(w.nt) * p.chunks + kc) * (kBlk / 16),
                        kBlk, &full[s]);
         }
         issued = i + 1;
       }
       if (!ok) atomicOr(p.err, kErrTmaTimeout);
       // no copy may still be landing when the CTA leaves: wait (bounded) for the last ones
-      for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
-        mbar_wait_bounded(&full[i & 1], (i >> 1) & 1, kWaitLimitNs);
+      for (int i = (issued > nst ? issued - nst : 0); i < issued; ++i)
+        mbar_wait_bounded(&full[i % nst], (i / nst) & 1, kWaitLimitNs);
     }
   } else if (warp == 5) {
     // ---- MMA issuer ----
     if (lane == 0) {
       for (int i = 0; i < nk && ok; ++i) {
-        const int s = i & 1;
+        const int s = i % nst;
         const int u = i / F, b = u & 1;              // fold unit and its partial region
         const bool unit_first = i % F == 0, unit_last = i % F == F - 1;
-        ok = mbar_wait_bounded(&full[s], (i >> 1) & 1, kWaitLimitNs);
+        ok = mbar_wait_bounded(&full[s], (i / nst) & 1, kWaitLimitNs);
         if (ok && unit_first && u >= 2) ok = mbar_wait_bounded(&pfree[b], ((u >> 1) - 1) & 1, kWaitLimitNs);
         if (!ok) break;
         tc_fence_after();
-        const unsigned char* st = smem + s * kStageBytes;
+        const unsigned char* st = smem + s * stage_bytes;
         const uint32_t dst = t_sum + kBN * (1 + b);
 #pragma unroll 1
         for (int ks = 0; ks < kBK / 16; ++ks) {
 #pragma unroll 1
           for (int t = 0; t < p.terms; ++t) {
             const uint64_t ad = smem_desc(st + c_terms[t][0] * kBlk + ks * 256);
-            const uint64_t bd = smem_desc(st + (3 + c_terms[t][1]) * kBlk + ks * 256);
+            const uint64_t bd = smem_desc(st + (planes + c_terms[t][1]) * kBlk + ks * 256);
             const unsigned acc = (!unit_first || ks > 0 || t > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -264,6 +268,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   } else {
     // ---- fold warps: S = S + P[chunk % 2]; an item's last chunk goes to global memory ----
     const uint32_t lanes = static_cast<uint32_t>(32 * warp) << 16;
+    float4* epi = reinterpret_cast<float4*>(smem + kStages * kStageBytes + 256) + warp * 32 * 8;
     for (int u = 0; u < nu; ++u) {
       const int b = u & 1;
       ok = __all_sync(0xffffffffu, mbar_wait_bounded(&ready[b], (u >> 1) & 1, kWaitLimitNs));   // warp-uniform
@@ -272,10 +277,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
       const int i = u * F;                  // the unit's first chunk
       const int kl = i % cpg;
       const bool first = kl == 0, last = kl + F == cpg;
-      float* drow = nullptr;
+      float* drow = nullptr;   // row 0 of the warp's 32 rows of the output tile
       if (last) {
         const GemmItem w = gemm_item(p, i / cpg);
-        drow = p.d + w.g * p.d_group + static_cast<size_t>(w.mt * kBM + 32 * warp + lane) * p.ldd + w.nt * kBN;
+        drow = p.d + w.g * p.d_group + static_cast<size_t>(w.mt * kBM + 32 * warp) * p.ldd + w.nt * kBN;
       }
 #pragma unroll 1
       for (int c = 0; c < kBN; c += 32) {
@@ -288,10 +293,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
           for (int k = 0; k < 32; ++k) x[k] = __float_as_uint(__fadd_rn(__uint_as_float(y[k]), __uint_as_float(x[k])));
         }
         if (last) {
+          // Lane l holds row l of the warp's 32 x 32 block. Transposed through shared memory
+          // (16-byte chunk j of row r at chunk j ^ (r & 7): both sides free of bank conflicts)
+          // so that each store instruction writes four rows of 128 contiguous bytes.
 #pragma unroll
-          for (int k = 0; k < 32; k += 4)
-            *reinterpret_cast<float4*>(drow + c + k) = make_float4(__uint_as_float(x[k]), __uint_as_float(x[k + 1]),
-                                                                   __uint_as_float(x[k + 2]), __uint_as_float(x[k + 3]));
+          for (int j = 0; j < 8; ++j)
+            epi[lane * 8 + (j ^ (lane & 7))] = make_float4(__uint_as_float(x[4 * j]), __uint_as_float(x[4 * j + 1]),
+                                                           __uint_as_float(x[4 * j + 2]), __uint_as_float(x[4 * j + 3]));
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = 4 * i + (lane >> 3), ch = lane & 7;
+            *reinterpret_cast<float4*>(drow + static_cast<size_t>(r) * p.ldd + c + 4 * ch) = epi[r * 8 + (ch ^ (r & 7))];
+          }
+          __syncwarp();   // the tile is read before the next block overwrites it
         } else {
           tmem_st32(t_sum + lanes + c, x);
         }
