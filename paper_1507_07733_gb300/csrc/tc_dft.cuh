@@ -79,7 +79,32 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
 }
 
 // the products kept, as (plane of A, plane of B), most significant first
-__constant__ int c_terms[6][2] = {{0, 0}, {0, 1}, {1, 0}, {0, 2}, {1, 1}, {2, 0}};
+// (0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)
+__host__ __device__ constexpr int term_a(int t) { return t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0; }
+__host__ __device__ constexpr int term_b(int t) { return t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0; }
+
+// The MMAs of one 64-wide K chunk held in the stage whose descriptor is base (A planes, then
+// B planes): for each 16-wide K step every kept product, accumulating into dst except at the
+// first MMA of a fold unit. Unrolled with the terms fixed, so each MMA's descriptors are the
+// base plus a constant.
+template <int TERMS>
+__device__ __forceinline__ void mma_chunk(uint64_t base, uint32_t dst, bool unit_first) {
+  constexpr int planes = TERMS == 6 ? 3 : 2;
+#pragma unroll
+  for (int ks = 0; ks < kBK / 16; ++ks) {
+#pragma unroll
+    for (int t = 0; t < TERMS; ++t) {
+      const uint64_t ad = base + ((term_a(t) * kBlk + ks * 256) >> 4);
+      const uint64_t bd = base + (((planes + term_b(t)) * kBlk + ks * 256) >> 4);
+      const unsigned acc = (unit_first && ks == 0 && t == 0) ? 0u : 1u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
+          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+          : "memory");
+    }
+  }
+}
 
 struct GemmParams {
   const uint4* a[3];       // BF16 planes of A, image [m_tiles][chunks] of 16 KB blocks
@@ -242,22 +267,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
         if (ok && unit_first && u >= 2) ok = mbar_wait_bounded(&pfree[b], ((u >> 1) - 1) & 1, kWaitLimitNs);
         if (!ok) break;
         tc_fence_after();
-        const unsigned char* st = smem + s * stage_bytes;
+        const uint64_t base = smem_desc(smem + s * stage_bytes);
         const uint32_t dst = t_sum + kBN * (1 + b);
-#pragma unroll 1
-        for (int ks = 0; ks < kBK / 16; ++ks) {
-#pragma unroll 1
-          for (int t = 0; t < p.terms; ++t) {
-            const uint64_t ad = smem_desc(st + c_terms[t][0] * kBlk + ks * 256);
-            const uint64_t bd = smem_desc(st + (planes + c_terms[t][1]) * kBlk + ks * 256);
-            const unsigned acc = (!unit_first || ks > 0 || t > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
-                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-                : "memory");
-          }
-        }
+        if (p.terms == 6) mma_chunk<6>(base, dst, unit_first);
+        else mma_chunk<3>(base, dst, unit_first);
         tc_commit(&empty[s]);                  // the stage may be refilled
         if (unit_last) tc_commit(&ready[b]);   // the partial region may be folded
       }
