@@ -770,7 +770,10 @@ ar_status ar_sync(ar_ctx* ctx, void* stream) {
   AR_CUDA(ctx, cudaMemcpy(&err, ctx->d_err, sizeof err, cudaMemcpyDeviceToHost));
   if (err) {
     AR_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
-    return fail(ctx, AR_ERR_DEVICE, "device error 0x%x (a bounded wait for a bulk copy ran out)", err);
+    return fail(ctx, AR_ERR_DEVICE,
+                "device error 0x%x (bit 0: a bounded wait for a bulk copy ran out; bit 1: a kernel got a launch "
+                "configuration it does not take)",
+                err);
   }
   return AR_OK;
 }
@@ -931,7 +934,9 @@ ar_status build_tc_tables(ar_ctx* ctx) {
       AR_CUDA(ctx, cudaMemcpy(ctx->tc_b[which][pl], img[pl].data(), bytes, cudaMemcpyHostToDevice));
     }
   }
-  AR_CUDA(ctx, cudaFuncSetAttribute(tc::split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  AR_CUDA(ctx, cudaFuncSetAttribute(tc::split_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(tc::kGemmSmem)));
+  AR_CUDA(ctx, cudaFuncSetAttribute(tc::split_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(tc::kGemmSmem)));
   return AR_OK;
 }
@@ -983,18 +988,27 @@ cudaError_t launch_gemm(ar_ctx* ctx, __nv_bfloat16* const (&a)[3], size_t m_pad,
   gp.ldd = n;
   gp.chunks = k / tc::kBK;
   gp.terms = terms;
-  const int tiles = static_cast<int>(m_pad / tc::kBM) * (n / tc::kBN);
   int groups = 1;
-  while (groups * 2 <= gp.chunks && tiles * groups * 2 <= 2 * ctx->num_sms) groups *= 2;
+  const int tiles128 = static_cast<int>(m_pad / tc::kBM) * (n / tc::kBN);
+  while (groups * 2 <= gp.chunks && tiles128 * groups * 2 <= 2 * ctx->num_sms) groups *= 2;
   gp.chunks_per_group = gp.chunks / groups;
+  // 256-wide tiles (half the MMA instructions and B-operand copies per flop) for the two-plane
+  // split when every item is a single fold unit of at most four chunks and enough tiles remain
+  const bool wide = terms == 3 && gp.chunks_per_group <= 4 && n % 256 == 0 &&
+                    static_cast<long long>(m_pad / tc::kBM) * (n / 256) >= 2 * ctx->num_sms;
+  const int bn = wide ? 256 : tc::kBN;
+  const int tiles = static_cast<int>(m_pad / tc::kBM) * (n / bn);
   gp.d = groups > 1 ? part : d;
   gp.d_group = m_pad * static_cast<size_t>(n);
   gp.m_tiles = static_cast<int>(m_pad / tc::kBM);
-  gp.n_tiles = n / tc::kBN;
+  gp.n_tiles = n / bn;
   gp.groups = groups;
   // persistent: one CTA per SM (the kernel's shared memory allows one), items strided
   const int items = tiles * groups;
-  tc::split_gemm_kernel<<<std::min(items, ctx->num_sms), tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
+  if (wide)
+    tc::split_gemm_kernel<256><<<std::min(items, ctx->num_sms), tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
+  else
+    tc::split_gemm_kernel<128><<<std::min(items, ctx->num_sms), tc::kGemmThreads, tc::kGemmSmem, stream>>>(gp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || groups == 1) return e;
   const size_t n4 = gp.d_group / 4;

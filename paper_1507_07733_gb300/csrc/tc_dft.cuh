@@ -68,8 +68,10 @@ __host__ __device__ constexpr size_t image_offset(int row, int k, int k_total) {
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kBN >> 3) << 17) |
-                            (uint32_t(kBM >> 4) << 24);
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+}
 
 // shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading byte offset >> 4
 // (bits 16-29), stride byte offset >> 4 (bits 32-45), version 1 (bits 46-47), no swizzle
@@ -83,24 +85,25 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
 __host__ __device__ constexpr int term_a(int t) { return t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0; }
 __host__ __device__ constexpr int term_b(int t) { return t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0; }
 
-// The MMAs of one 64-wide K chunk held in the stage whose descriptor is base (A planes, then
-// B planes): for each 16-wide K step every kept product, accumulating into dst except at the
-// first MMA of a fold unit. Unrolled with the terms fixed, so each MMA's descriptors are the
-// base plus a constant.
-template <int TERMS>
+// The MMAs of one 64-wide K chunk held in the stage whose descriptor is base (A planes of
+// 128 rows, then B planes of BN rows): for each 16-wide K step every kept product,
+// accumulating into dst except at the first MMA of a fold unit. Unrolled with the terms
+// fixed, so each MMA's descriptors are the base plus a constant.
+template <int TERMS, int BN>
 __device__ __forceinline__ void mma_chunk(uint64_t base, uint32_t dst, bool unit_first) {
   constexpr int planes = TERMS == 6 ? 3 : 2;
+  constexpr uint32_t id = idesc<BN>();
 #pragma unroll
   for (int ks = 0; ks < kBK / 16; ++ks) {
 #pragma unroll
     for (int t = 0; t < TERMS; ++t) {
       const uint64_t ad = base + ((term_a(t) * kBlk + ks * 256) >> 4);
-      const uint64_t bd = base + (((planes + term_b(t)) * kBlk + ks * 256) >> 4);
+      const uint64_t bd = base + ((planes * kBlk + term_b(t) * (BN / 128) * kBlk + ks * 256) >> 4);
       const unsigned acc = (unit_first && ks == 0 && t == 0) ? 0u : 1u;
       asm volatile(
           "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
           " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
-          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+          "l"(ad), "l"(bd), "r"(id), "r"(acc)
           : "memory");
     }
   }
@@ -183,13 +186,18 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 
 // Accumulation. The tensor cores' FP32 accumulator loses about 2^-26 of relative precision,
 // with a bias, at every MMA (measured: the error grows linearly with the number of MMAs into
-// one accumulator), so each fold unit (one or two 64-wide K chunks) is accumulated on its own
+// one accumulator), so each fold unit (up to four 64-wide K chunks) is accumulated on its own
 // into a partial region P[unit % 2] of tensor memory, and warps 0-3 fold it into the running
 // sum S with IEEE round-to-nearest FP32 additions, in order: S = (((P0 + P1) + P2) + ...).
 // With two partial regions the MMAs of one unit overlap the fold of the previous one.
-constexpr int kTmemCols = 512;   // S, P0, P1: 128 columns each, rounded up to a power of two
+// BN = 128: S, P0, P1 of 128 columns each; BN = 256 (x3 items of at most four chunks, which
+// are single fold units and need no S): P0, P1 of 256 columns.
+constexpr int kTmemCols = 512;
 
+template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __grid_constant__ GemmParams p) {
+  static_assert(BN == 128 || BN == 256, "tile width");
+  constexpr int NB = BN / 128;   // 128-row B blocks per tile
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* full = bars;          // [3] stage filled (bulk copies complete)
@@ -207,14 +215,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
   const int cpg = p.chunks_per_group;
   const int nk = my_items * cpg;
   const int planes = p.terms == 6 ? 3 : 2;
-  // The stage ring: two stages of 3 + 3 planes, or three of 2 + 2 planes, in the same bytes.
-  const int nst = planes == 2 ? 3 : 2;
-  const unsigned stage_bytes = 2u * planes * kBlk;
+  // The stage ring in the same 192 KB: three stages of 2 + 2 blocks (x3, BN 128), two of
+  // 3 + 3 (x6, BN 128) or two of 2 + 4 (x3, BN 256).
+  const unsigned stage_bytes = static_cast<unsigned>(planes * (1 + NB)) * kBlk;
+  const int nst = min(3, static_cast<int>(kStages * kStageBytes / stage_bytes));
   // Chunks per fold: up to 4 (K = 256 accumulated on the tensor cores between folds), a
   // divisor of the item's chunk count; an item of at most 4 chunks is one fold unit, whose
   // fold only moves the accumulator to global memory.
   const int F = cpg <= 4 ? cpg : cpg % 4 == 0 ? 4 : cpg % 2 == 0 ? 2 : 1;
   const int nu = nk / F;   // fold units
+  if (NB == 2 && (F != cpg || planes != 2)) {   // the wide tile has no running sum and room for 2 planes
+    if (tid == 0) atomicOr(p.err, kErrBadLaunch);
+    return;
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_s)),
@@ -242,12 +255,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
         const GemmItem w = gemm_item(p, i / cpg);
         const int kc = w.g * cpg + i % cpg;
         unsigned char* st = smem + s * stage_bytes;
-        mbar_arrive_expect_tx(&full[s], 2u * planes * kBlk);
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
         for (int pl = 0; pl < planes; ++pl) {
           tma_bulk_g2s(st + pl * kBlk, p.a[pl] + (static_cast<size_t>(w.mt) * p.chunks + kc) * (kBlk / 16), kBlk,
                        &full[s]);
-          tma_bulk_g2s(st + (planes + pl) * kBlk, p.b[pl] + (static_cast<size_t>(w.nt) * p.chunks + kc) * (kBlk / 16),
-                       kBlk, &full[s]);
+          // the tile's NB consecutive 128-row B blocks: rows of the wider MMA continue in order
+          for (int h = 0; h < NB; ++h)
+            tma_bulk_g2s(st + (planes + pl * NB + h) * kBlk,
+                         p.b[pl] + (static_cast<size_t>(w.nt * NB + h) * p.chunks + kc) * (kBlk / 16), kBlk, &full[s]);
         }
         issued = i + 1;
       }
@@ -268,9 +283,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
         if (!ok) break;
         tc_fence_after();
         const uint64_t base = smem_desc(smem + s * stage_bytes);
-        const uint32_t dst = t_sum + kBN * (1 + b);
-        if (p.terms == 6) mma_chunk<6>(base, dst, unit_first);
-        else mma_chunk<3>(base, dst, unit_first);
+        const uint32_t dst = t_sum + (NB == 2 ? BN * b : BN * (1 + b));
+        if (p.terms == 6) mma_chunk<6, BN>(base, dst, unit_first);
+        else mma_chunk<3, BN>(base, dst, unit_first);
         tc_commit(&empty[s]);                  // the stage may be refilled
         if (unit_last) tc_commit(&ready[b]);   // the partial region may be folded
       }
@@ -293,12 +308,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) split_gemm_kernel(const __gri
       float* drow = nullptr;   // row 0 of the warp's 32 rows of the output tile
       if (last) {
         const GemmItem w = gemm_item(p, i / cpg);
-        drow = p.d + w.g * p.d_group + static_cast<size_t>(w.mt * kBM + 32 * warp) * p.ldd + w.nt * kBN;
+        drow = p.d + w.g * p.d_group + static_cast<size_t>(w.mt * kBM + 32 * warp) * p.ldd + w.nt * BN;
       }
+      const uint32_t preg = t_sum + (NB == 2 ? BN * b : BN * (1 + b));
 #pragma unroll 1
-      for (int c = 0; c < kBN; c += 32) {
+      for (int c = 0; c < BN; c += 32) {
         uint32_t x[32], y[32];
-        tmem_ld32(t_sum + kBN * (1 + b) + lanes + c, x);
+        tmem_ld32(preg + lanes + c, x);
         if (!first) tmem_ld32(t_sum + lanes + c, y);
         tmem_wait_ld();
         if (!first) {
