@@ -37,7 +37,6 @@ constexpr unsigned kStBadDir = 4u;
 constexpr unsigned kStBadPattern = 8u;
 
 constexpr unsigned kErrTmaTimeout = 1u;     // a bounded mbarrier wait ran out
-constexpr unsigned kErrBadLaunch = 2u;      // a kernel was launched with a configuration it does not take
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
 
 // ---- shapes per trace length ------------------------------------------------------------

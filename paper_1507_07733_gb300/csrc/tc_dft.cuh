@@ -48,6 +48,7 @@ namespace tc {
 constexpr int kSub = 512;                         // sub-block length
 constexpr int kBandPhase = 128;                   // band bins per sub-block phase j1 (M / A)
 constexpr int kBM = 128, kBN = 128, kBK = 64;     // CTA tile and K chunk
+constexpr unsigned kErrBadLaunch = 2u;           // device error bit: a launch configuration the GEMM does not take
 constexpr unsigned kBlk = kBM * kBK * 2;          // bytes of one BF16 plane of a 128 x 64 block (16 KB)
 constexpr unsigned kStageBytes = 6 * kBlk;        // A and B, up to 3 planes each
 constexpr int kStages = 2;                          // ring bytes: 2 such stages (x6) or 3 of 4 blocks (x3)
