@@ -1034,12 +1034,13 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   tc::tc_forward_pre_kernel<N_><<<2 * S, tc::kSub, 0, stream>>>(ev, fimg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_gemm(ctx, w.fa, rows_f, 0, terms, w.xf, w.part, stream)) != cudaSuccess) return e;
-  const size_t solve_smem = sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
+  // per-bin inverses [2][N/4] float4, then the node scratch [n_f][8] float2
+  const size_t solve_smem = 2 * sizeof(float4) * (N_ / 4) + sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
     // several pairs per CTA share the interpolation, as long as two CTAs per SM remain
     const int ppc = std::max(1, std::min(tc::kSolvePairsMax, np / (2 * ctx->num_sms)));
-    tc::tc_solve_kernel<N_><<<(np + ppc - 1) / ppc, 256, solve_smem, stream>>>(
+    tc::tc_solve_kernel<N_><<<(np + ppc - 1) / ppc, tc::kSolveThreads, solve_smem, stream>>>(
         ev, reinterpret_cast<const float2*>(w.xf), zimg, p0, np, ppc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (prof && p0 == 0 && (e = cudaEventRecord(ctx->ev[1], stream)) != cudaSuccess) return e;

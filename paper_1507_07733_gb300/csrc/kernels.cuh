@@ -668,11 +668,13 @@ __device__ __forceinline__ void issue_key(const EventDesc& ev, int d, int p, Dir
 // scaled inverse, H^-1 * 2/N (the 2/N of the one-sided inverse transform, Sec. 3), into hinv.
 // Returns whether any bin of the band was singular. Bins outside the pattern's frequency
 // range, singular bins and keys with a bad direction or pattern get a zero inverse.
-template <int N_>
+// T: the CTA's threads; direct: the corners are read from the table (else from slab).
+template <int N_, int T = Layout<N_>::T>
 __device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const DirInfo& di, const float2* slab,
-                                              float2* hn, float4* hinv) {
+                                              bool direct, float2* hn, float4* hinv) {
   using L = Layout<N_>;
-  constexpr int M = L::M, T = L::T, NB = M / T;
+  constexpr int M = L::M, NB = M / T;
+  static_assert(M % T == 0, "bins per thread");
   constexpr float kScale = 2.0f / static_cast<float>(L::N);
   const int tid = threadIdx.x;
   const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
@@ -680,7 +682,6 @@ __device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const 
   if (valid) {
     const int n_f = pr.n_f;
     const size_t node = static_cast<size_t>(n_f) * 4;
-    const bool direct = ev.slab_direct != 0;
     const float2* c0 = pr.table + di.slab0 * node;
     const float2* c1 = pr.table + di.slab1 * node;
     const float2* c2 = pr.table + di.slab2 * node;
@@ -873,7 +874,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       di = *sdir;
       if (tid == 0) tma_bulk_wait_read();
       __syncthreads();
-      key_sing = build_inverse<N_>(ev, p, di, slab, hn, hinv);
+      key_sing = build_inverse<N_>(ev, p, di, slab, ev.slab_direct != 0, hn, hinv);
       cur_e = e;
       cur_d = d;
       cur_p = p;

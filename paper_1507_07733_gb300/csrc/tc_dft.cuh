@@ -400,28 +400,33 @@ __global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_const
   }
 }
 
-// ---- per pair: VEL interpolation and 2x2 solve (as the FP32 path) -> inverse GEMM rows ----
-// One CTA per pairs_per_cta consecutive pairs of the chunk [pair0, pair0 + n_pairs), the
-// interpolation redone where the direction or the pattern changes; the forward GEMM output holds
-// X_c[k_lo + j1 + A j2] at row ((s * 2 + c) * A + j1), complex column j2. Writes Zf as GEMM row
-// ((lp * 2 + pol) * A + j1), complex column j2, into the inverse GEMM's A image.
+// ---- per pair: 2x2 solve (as the FP32 path) -> inverse GEMM rows --------------------------
+// One CTA per pairs_per_cta consecutive pairs of the chunk [pair0, pair0 + n_pairs). Where the
+// direction or the pattern changes, the CTA forms the scaled per-bin inverse of the VEL
+// matrix in shared memory (build_inverse: corners read from the L2-resident table); each pair
+// then applies it to its station's spectrum. The forward GEMM output holds X_c[k_lo + j1 + A j2]
+// at row ((s * 2 + c) * A + j1), complex column j2. Zf goes to rows ((lp * 2 + pol) * A + j1),
+// complex column j2, of the inverse GEMM's A image. Thread i takes column j2 = 4 (i / 4A) +
+// i % 4 and row j1 = (i / 4) % A, so that a warp's stores fill whole 16-byte rows of the
+// image's 8 x 8 core matrices (A rows of 16 bytes in a row for each polarisation).
 constexpr int kSolvePairsMax = 8;   // pairs per solve CTA (consecutive: mostly one direction)
+constexpr int kSolveThreads = 256;
 
 template <int N_>
-__global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ EventDesc ev, const float2* xf,
-                                                       const __grid_constant__ SplitImage img, long long pair0,
-                                                       int n_pairs, int pairs_per_cta) {
-  constexpr int N = N_, M = N / 4, A = N / kSub;
+__global__ void __launch_bounds__(kSolveThreads) tc_solve_kernel(const __grid_constant__ EventDesc ev,
+                                                                 const float2* xf,
+                                                                 const __grid_constant__ SplitImage img,
+                                                                 long long pair0, int n_pairs, int pairs_per_cta) {
+  constexpr int N = N_, M = N / 4, A = N / kSub, T = kSolveThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* hn = reinterpret_cast<float2*>(smem_raw);   // [n_f][8]: 4 values, 4 slopes
+  float4* hinv = reinterpret_cast<float4*>(smem_raw);                         // [2][M]
+  float2* hn = reinterpret_cast<float2*>(smem_raw + 2 * sizeof(float4) * M);  // [n_f][8]
   __shared__ DirInfo s_di;
-  __shared__ PatternRef s_pr;
   const int tid = threadIdx.x;
   const int S = ev.n_st;
-  constexpr float kScale = 2.0f / static_cast<float>(N);
   int cur_d = -1, cur_p = -3;
   DirInfo di;
-  PatternRef pr;
+  bool key_sing = false;
   for (int k = 0; k < pairs_per_cta; ++k) {
     const int lp = blockIdx.x * pairs_per_cta + k;   // pair within the chunk
     if (lp >= n_pairs) break;
@@ -430,70 +435,33 @@ __global__ void __launch_bounds__(256) tc_solve_kernel(const __grid_constant__ E
     const int p = station_pattern(ev, s);
     if (d != cur_d || p != cur_p) {
       // new direction or pattern: the cell (FP64) by one thread (FP64 is a small fraction of
-      // the FP32 rate), then the angular interpolation per frequency node
-      __syncthreads();   // the previous pair's reads of hn are done
-      if (tid == 0) s_di = pair_cell(ev, d, p, &s_pr);
+      // the FP32 rate), then the per-bin inverse
+      __syncthreads();   // the previous pair's reads of hinv are done
+      if (tid == 0) s_di = pair_cell(ev, d, p, nullptr);
       __syncthreads();
       di = s_di;
-      pr = s_pr;
-      const int n_f = di.pat == -2 ? 0 : pr.n_f;
-      const size_t node = static_cast<size_t>(pr.n_f) * 4;
-      const auto bilin = [&](int x) {
-        const float2 a = __ldg(pr.table + di.slab0 * node + x), b = __ldg(pr.table + di.slab1 * node + x);
-        const float2 c = __ldg(pr.table + di.slab2 * node + x), dd = __ldg(pr.table + di.slab3 * node + x);
-        float2 h;
-        h.x = fmaf(di.w[3], dd.x, fmaf(di.w[2], c.x, fmaf(di.w[1], b.x, di.w[0] * a.x)));
-        h.y = fmaf(di.w[3], dd.y, fmaf(di.w[2], c.y, fmaf(di.w[1], b.y, di.w[0] * a.y)));
-        return h;
-      };
-      for (int x = tid; x < n_f * 4; x += blockDim.x) {
-        const int f = x >> 2, cp = x & 3;
-        const float2 h = bilin(x);
-        const float2 h1 = f + 1 < n_f ? bilin(x + 4) : h;
-        hn[8 * f + cp] = h;
-        hn[8 * f + 4 + cp] = csub(h1, h);
-      }
-      __syncthreads();
+      key_sing = build_inverse<N_, T>(ev, p, di, nullptr, true, hn, hinv);
       cur_d = d;
       cur_p = p;
     }
-    const bool valid = (di.st & (kStBadDir | kStBadPattern)) == 0;
-    bool sing = false;
     const float2* x0 = xf + static_cast<size_t>(s * 2) * A * kBandPhase;
     const float2* x1 = x0 + A * kBandPhase;
-    for (int i = tid; i < M; i += blockDim.x) {   // i = j1 * 128 + j2
-      const int j1 = i / kBandPhase, j2 = i % kBandPhase;
+#pragma unroll
+    for (int it = 0; it < M / T; ++it) {
+      const int i = tid + T * it;
+      const int j1 = (i / 4) % A, j2 = 4 * (i / (4 * A)) + i % 4;
       const int j = j1 + A * j2;
-      const int2 bf = __ldg(pr.binf + j);
-      float2 et = make_float2(0.f, 0.f), ep = et;
-      if (bf.x >= 0 && valid) {
-        const float tf = __int_as_float(bf.y);
-        const float4* h0 = reinterpret_cast<const float4*>(hn + 8 * bf.x);
-        const float4 h01 = h0[0], h23 = h0[1], g01 = h0[2], g23 = h0[3];
-        const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));
-        const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));
-        const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));
-        const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));
-        const float2 v0 = x0[i], v1 = x1[i];
-        const float2 det = csub(cmul(a, dd), cmul(b, c));
-        const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
-        const float dd2 = cabs2(det);
-        if (dd2 > 1e-12f * sc * sc) {
-          const float inv = kScale * rcp_approx(dd2);
-          const float2 nt = csub(cmul(dd, v0), cmul(b, v1));
-          const float2 np = csub(cmul(a, v1), cmul(c, v0));
-          const float2 ct = cmulc(nt, det), cpp = cmulc(np, det);
-          et = make_float2(ct.x * inv, ct.y * inv);
-          ep = make_float2(cpp.x * inv, cpp.y * inv);
-        } else {
-          sing = true;
-        }
-      }
+      const float4 h0 = hinv[j], h1 = hinv[M + j];   // (h00, h01), (h10, h11)
+      const float2 v0 = x0[j1 * kBandPhase + j2], v1 = x1[j1 * kBandPhase + j2];
+      float2 et, ep;
+      et.x = fmaf(h0.z, v1.x, fmaf(-h0.w, v1.y, fmaf(h0.x, v0.x, -h0.y * v0.y)));
+      et.y = fmaf(h0.z, v1.y, fmaf(h0.w, v1.x, fmaf(h0.x, v0.y, h0.y * v0.x)));
+      ep.x = fmaf(h1.z, v1.x, fmaf(-h1.w, v1.y, fmaf(h1.x, v0.x, -h1.y * v0.y)));
+      ep.y = fmaf(h1.z, v1.y, fmaf(h1.w, v1.x, fmaf(h1.x, v0.y, h1.y * v0.x)));
       put_split(img.plane, img.planes, image_offset((lp * 2) * A + j1, 2 * j2, kInvK), et);
       put_split(img.plane, img.planes, image_offset((lp * 2 + 1) * A + j1, 2 * j2, kInvK), ep);
     }
-    const bool any = __syncthreads_or(sing);
-    if (tid == 0) ev.status[pair] = di.st | (any ? kStSingular : 0u);
+    if (tid == 0) ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
   }
 }
 
