@@ -314,6 +314,7 @@ def run_gpu(args):
     mixed = run_mixed_antennas(binding, synth, ctx, dev, stream, peaks.get("hbm_gbs"))
     refine = run_output_variant(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"), "fine")
     weighted = run_output_variant(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"), "snr")
+    lengths = run_trace_lengths(binding, synth, ctx, pid, dev, stream, peaks.get("hbm_gbs"))
 
     batched = None
     if not args.no_batch:
@@ -358,6 +359,7 @@ def run_gpu(args):
             "mixed_antennas": mixed,
             "peak_refinement": refine,
             "snr_weighting": weighted,
+            "trace_lengths": lengths,
             "batched_uneven": batched,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -594,6 +596,47 @@ def run_back_to_back(binding, ctx, es, ost, pairs, stream, reps=200):
     ms = a.elapsed_time(b) / reps
     return {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4), "calls": reps,
             "note": "no L2 flush between calls"}
+
+
+def run_trace_lengths(binding, synth, ctx, pid, dev, stream, hbm=None, reps=100):
+    """The scan's geometry (124 stations x 64 directions) at the other supported trace
+    lengths, 1024 and 4096 samples: device time per call back to back, unfolds/s and the
+    unfold kernel's HBM fraction (algorithmic bytes over the kernel's CUDA-event time)."""
+    import torch
+    res = {}
+    for n in (1024, 4096):
+        ev = synth.direction_scan(n_samples=n)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        keep = (t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))
+        es = binding.make_event(pid, *keep, ev.fs_hz)
+        out, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, n, device=dev)
+        fn = lambda: binding.ar_unfold(ctx.h, es, ost, stream.cuda_stream)
+        for _ in range(10):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        ctx.sync(stream)
+        ms = a.elapsed_time(b) / reps
+        binding.ar_set_profiling(ctx.h, 1)
+        kk = []
+        for _ in range(20):
+            fn()
+            ctx.sync(stream)
+            kk.append(binding.ar_kernel_times(ctx.h)[1])
+        binding.ar_set_profiling(ctx.h, 0)
+        k_ms = statistics.mean(kk)
+        pairs = ev.n_stations * ev.n_dirs
+        row = {"unfolds_per_s": round(pairs / (ms * 1e-3), 1), "ms_per_call": round(ms, 4),
+               "unfold_kernel_ms": round(k_ms, 4)}
+        if hbm:
+            nbytes = unfold_bytes_per_launch(ev.n_stations, ev.n_dirs, n, 51)
+            row["hbm_frac"] = round(nbytes / (k_ms * 1e-3) / 1e9 / hbm, 3)
+        res[str(n)] = row
+        del keep, out, ost
+    return res
 
 
 def run_mixed_antennas(binding, synth, ctx, dev, stream, hbm=None, reps=100):
