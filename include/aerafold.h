@@ -273,8 +273,9 @@ ar_status ar_batch_run(ar_batch* plan, const ar_event* events, const ar_outputs*
                        void* stream);
 
 /* Chosen unfold CTAs per SM for the 1024-, 2048- and 4096-sample classes (ctas_per_sm[3]),
- * and the autotuner's measured graph time in ms for 1..4 CTAs per SM (candidate_ms[4], 0 if
- * not tried; may be NULL). */
+ * and the autotuner's measured graph time in ms for 1..6 CTAs per SM (candidate_ms[6], 0 if
+ * not tried, e.g. beyond what every class can hold; may be NULL). A candidate k runs each
+ * class at min(k, the most CTAs per SM it can hold). */
 ar_status ar_batch_tuning(const ar_batch* plan, int32_t* ctas_per_sm, float* candidate_ms);
 
 /* Wait for the plan's runs in flight and free it. NULL is a no-op. */

@@ -234,9 +234,9 @@ def ar_batch_run(ctx, plan, events, outs, stream: int = 0) -> None:
 
 
 def ar_batch_tuning(plan):
-    """(CTAs per SM for the 1024/2048/4096 classes, autotuner graph ms for 1..4 CTAs per SM)."""
+    """(CTAs per SM for the 1024/2048/4096 classes, autotuner graph ms for 1..6 CTAs per SM)."""
     c = (ctypes.c_int32 * 3)()
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 6)()
     st = load().ar_batch_tuning(plan, c, ms)
     if st != AR_OK:
         raise ArError(st, "ar_batch_tuning")

@@ -1132,6 +1132,8 @@ namespace {
 constexpr int kClasses = 3;
 int class_of(int n) { return n == 1024 ? 0 : n == 2048 ? 1 : 2; }
 
+constexpr int kTuneMax = 6;   // the batch autotuner tries 1..kTuneMax unfold CTAs per SM
+
 }  // namespace
 
 struct ar_batch {
@@ -1151,7 +1153,7 @@ struct ar_batch {
   int max_ctas_per_sm[kClasses] = {0, 0, 0};
   int slab_direct[kClasses] = {0, 0, 0};       // corner slabs read from L2 where staging them costs occupancy
   bool tuned = false;
-  float tune_ms[5] = {0, 0, 0, 0, 0};          // graph time per candidate (autotune)
+  float tune_ms[kTuneMax + 1] = {};            // graph time per candidate CTAs per SM (autotune)
 };
 
 namespace {
@@ -1368,7 +1370,7 @@ static ar_status batch_autotune(ar_batch* b, int set, bool snr, cudaStream_t str
   AR_CUDA(ctx, cudaEventCreate(&t0));
   AR_CUDA(ctx, cudaEventCreate(&t1));
   const int kmax = std::max(b->max_ctas_per_sm[0], std::max(b->max_ctas_per_sm[1], b->max_ctas_per_sm[2]));
-  for (int k = 1; k <= kmax && k <= 4; ++k) {
+  for (int k = 1; k <= kmax && k <= kTuneMax; ++k) {
     int ctas[kClasses];
     for (int c = 0; c < kClasses; ++c) ctas[c] = std::min(k, b->max_ctas_per_sm[c]);
     cudaGraphExec_t g = nullptr;
@@ -1440,7 +1442,7 @@ ar_status ar_batch_tuning(const ar_batch* b, int32_t* ctas_per_sm, float* candid
   if (!b || !ctas_per_sm) return AR_ERR_INVALID_ARG;
   for (int c = 0; c < kClasses; ++c) ctas_per_sm[c] = b->ctas_per_sm[c];
   if (candidate_ms)
-    for (int k = 0; k < 4; ++k) candidate_ms[k] = b->tune_ms[k + 1];
+    for (int k = 0; k < kTuneMax; ++k) candidate_ms[k] = b->tune_ms[k + 1];
   return AR_OK;
 }
 

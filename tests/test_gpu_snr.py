@@ -140,3 +140,24 @@ def test_snr_on_the_tensor_core_host_batch_and_server_paths(env):
     for k, v in sout.items():
         assert np.array_equal(v.numpy(), dev[k]), k
     srv.close()
+
+
+def test_batch_switches_between_the_two_instantiations(env):
+    """A batch plan run without SNRs, with them, and without again (one captured graph per
+    instantiation): every run equals the plain calls bit for bit."""
+    binding, ctx, pat, pid = env
+    evs = [synth.make_event(20, 2048, synth.scan_directions(2, 2), seed_key=1420),
+           synth.make_event(9, 1024, synth.scan_directions(3, 1), seed_key=1421)]
+    keep = [(_dev(e.traces), _dev(e.pos_m), _dev(e.t_start_ns), _dev(e.dirs_rad)) for e in evs]
+    structs = [binding.make_event(pid, *k, e.fs_hz) for k, e in zip(keep, evs)]
+    b = ctx.batch(2, 40, 8, max_n_freq=64)
+    for snr in (False, True, False):
+        outs = [binding.alloc_outputs(e.n_dirs, e.n_stations, e.n_samples, device="cuda", snr=snr)[0] for e in evs]
+        b.run(structs, outs)
+        torch.cuda.synchronize()
+        for e, k, o in zip(evs, keep, outs):
+            ref, _ = binding.alloc_outputs(e.n_dirs, e.n_stations, e.n_samples, device="cuda", snr=snr)
+            ctx.unfold(pid, *k, e.fs_hz, out=ref, sync=True)
+            for k, v in o.items():
+                assert np.array_equal(v.cpu().numpy(), ref[k].cpu().numpy()), (snr, k)
+    b.close()
