@@ -135,3 +135,31 @@ def test_x3_and_x6_on_the_scan_in_the_benchmark_configuration(env):
         for d in range(0, ev.n_dirs, 9):
             r, t0, chi2 = oracle.residual(ev.pos_m, gpu["peak_time_ns"][d], *ev.dirs_rad[d])
             assert np.allclose(gpu["residual_ns"][d], r, rtol=0, atol=1e-9 * max(1.0, np.abs(r).max()))
+
+
+def test_fine_times_and_snr_on_the_scan(env):
+    """The scan through the tensor-core path with sub-sample times and SNRs: peaks only equals
+    full outputs bit for bit, and the times and SNRs agree with the FP32 path to the x6
+    precision."""
+    binding, ctx, pat, pid = env
+    ev = synth.direction_scan()
+    args = (pid, _dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns), _dev(ev.dirs_rad))
+    res = {}
+    for traces in (True, False):
+        out, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device="cuda", traces=traces,
+                                       fine=True, snr=True)
+        ctx.unfold_tc(*args, split_terms=6, fs_hz=ev.fs_hz, out=out, sync=True)
+        res[traces] = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    for k in ("peak_idx", "peak_amp", "peak_time_ns", "peak_time_fine_ns", "snr", "residual_ns", "t0_ns", "chi2",
+              "status"):
+        assert np.array_equal(res[True][k], res[False][k]), k
+    fp, _ = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device="cuda", fine=True, snr=True)
+    ctx.unfold(*args, ev.fs_hz, out=fp, sync=True)
+    fp = {k: v.cpu().numpy() for k, v in fp.items()}
+    tc = res[True]
+    same = tc["peak_idx"] == fp["peak_idx"]
+    assert same.mean() > 0.999
+    assert np.all(abs(tc["peak_time_fine_ns"][same] - fp["peak_time_fine_ns"][same]) <= 0.01 * 5.0)
+    assert np.all(abs(tc["snr"][same] - fp["snr"][same]) <= 1e-4 * fp["snr"][same])
+    e = rel_l2(tc["envelope"], fp["envelope"], ev.n_samples)
+    assert e.max() <= 1e-5, e.max()
