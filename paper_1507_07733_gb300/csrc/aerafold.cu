@@ -1036,10 +1036,17 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
   if ((e = launch_gemm(ctx, w.fa, rows_f, 0, terms, w.xf, w.part, stream)) != cudaSuccess) return e;
   // per-bin inverses [2][N/4] float4, then the node scratch [n_f][8] float2
   const size_t solve_smem = 2 * sizeof(float4) * (N_ / 4) + sizeof(float2) * 8 * static_cast<size_t>(ev.n_f_layout);
+  int solve_per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&solve_per_sm, tc::tc_solve_kernel<N_>, tc::kSolveThreads,
+                                                         solve_smem)) != cudaSuccess)
+    return e;
+  const long long solve_slots = std::max(1, solve_per_sm) * static_cast<long long>(ctx->num_sms);
   for (long long p0 = 0; p0 < pairs; p0 += chunk) {
     const int np = static_cast<int>(std::min(chunk, pairs - p0));
-    // several pairs per CTA share the interpolation, as long as two CTAs per SM remain
-    const int ppc = std::max(1, std::min(tc::kSolvePairsMax, np / (2 * ctx->num_sms)));
+    // several pairs per CTA share the per-bin inverse: just enough that the CTAs fit in one
+    // wave of resident CTAs (a second, partial wave would double the time)
+    const int ppc = static_cast<int>(
+        std::max<long long>(1, std::min<long long>(tc::kSolvePairsMax, (np + solve_slots - 1) / solve_slots)));
     tc::tc_solve_kernel<N_><<<(np + ppc - 1) / ppc, tc::kSolveThreads, solve_smem, stream>>>(
         ev, reinterpret_cast<const float2*>(w.xf), zimg, p0, np, ppc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

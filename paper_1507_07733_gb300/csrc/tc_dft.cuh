@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kSub) tc_forward_pre_kernel(const __grid_const
 // complex column j2, of the inverse GEMM's A image. Thread i takes column j2 = 4 (i / 4A) +
 // i % 4 and row j1 = (i / 4) % A, so that a warp's stores fill whole 16-byte rows of the
 // image's 8 x 8 core matrices (A rows of 16 bytes in a row for each polarisation).
-constexpr int kSolvePairsMax = 8;   // pairs per solve CTA (consecutive: mostly one direction)
+constexpr int kSolvePairsMax = 32;   // pairs per solve CTA (consecutive: mostly one direction)
 constexpr int kSolveThreads = 256;
 
 template <int N_>
