@@ -73,6 +73,7 @@ struct ar_ctx {
   float4* spec = nullptr;
   size_t spec_bytes = 0;
   unsigned* dir_done = nullptr;   // [max directions] completion counters of the fused residual
+  DirPre* dir_pre = nullptr;      // [max directions] cells and source vectors, formed per launch
   size_t dir_cap = 0;
   unsigned char* recon = nullptr; // reconstruction state, station times and indices
   size_t recon_bytes = 0;
@@ -280,12 +281,15 @@ ar_status ensure_dirs(ar_ctx* ctx, size_t n_dir) {
   if (ctx->dir_done) {
     AR_CUDA(ctx, cudaDeviceSynchronize());
     AR_CUDA(ctx, cudaFree(ctx->dir_done));
+    AR_CUDA(ctx, cudaFree(ctx->dir_pre));
     ctx->dir_done = nullptr;
+    ctx->dir_pre = nullptr;
     ctx->dir_cap = 0;
   }
   const size_t cap = std::max<size_t>(n_dir, 256);
   AR_CUDA(ctx, cudaMalloc(&ctx->dir_done, cap * sizeof(unsigned)));
   AR_CUDA(ctx, cudaMemset(ctx->dir_done, 0, cap * sizeof(unsigned)));
+  AR_CUDA(ctx, cudaMalloc(&ctx->dir_pre, cap * sizeof(DirPre)));
   ctx->dir_cap = cap;
   return AR_OK;
 }
@@ -406,6 +410,7 @@ struct PathBuffers {      // library-side buffers one launch of the path uses
   const float2* t1;
   const float2* wn;
   const int2* binf;
+  DirPre* dir_pre = nullptr;   // [D] per-direction precomputation by the station kernel, or none
 };
 
 // the kernels' view of one event (see EventDesc)
@@ -429,6 +434,7 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.chi2 = out->chi2;
   d.spec = b.spec;
   d.dir_done = b.dir_done;
+  d.dir_pre = b.dir_pre;
   d.table = table;
   d.binf = b.binf;
   d.t1 = b.t1;
@@ -486,7 +492,7 @@ template <int N_>
 ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, const Resolved& rs,
                      cudaStream_t stream) {
   const PatternDev& pat = ctx->patterns[ev->pattern_id];
-  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
+  PathBuffers b{ctx->spec, ctx->dir_done, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf, ctx->dir_pre};
   EventDesc desc = make_desc(b, pat.desc, pat.table, ev, out, rs.k_lo);
   ar_status st = attach_patterns(ctx, ev, rs.k_lo, &desc);
   if (st != AR_OK) return st;
@@ -588,6 +594,7 @@ ar_status ar_destroy(ar_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   cudaFree(ctx->spec);
   cudaFree(ctx->dir_done);
+  cudaFree(ctx->dir_pre);
   cudaFree(ctx->recon);
   for (auto& m : ctx->tc_b)
     for (auto* p : m) cudaFree(p);
@@ -1152,6 +1159,7 @@ struct ar_batch {
   float4* spec = nullptr;                      // station spectra of all events
   size_t spec_bytes = 0;
   unsigned* dir_done = nullptr;
+  DirPre* dir_pre = nullptr;
   cudaGraphExec_t exec[2][2] = {};            // [staging set][with SNRs], built when first needed
   cudaEvent_t done[2] = {nullptr, nullptr};
   bool pending[2] = {false, false};
@@ -1256,7 +1264,7 @@ ar_status batch_fill(ar_batch* b, int set, const ar_event* events, const ar_outp
                   b->lim.max_stations, dirs, b->lim.max_dirs);
     const int c = class_of(ev->n_samples);
     PathBuffers pb{reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(b->spec) + spec_off),
-                   b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf};
+                   b->dir_done + dir_off, ctx->d_err, rs.lt->t1, rs.lt->wn, rs.binf, b->dir_pre + dir_off};
     const PatternDev& pat = ctx->patterns[ev->pattern_id];
     EventDesc d = make_desc(pb, pat.desc, pat.table, ev, &outs[i], rs.k_lo);
     if ((st = attach_patterns(ctx, ev, rs.k_lo, &d)) != AR_OK) return st;
@@ -1302,6 +1310,7 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
   if (e == cudaSuccess) e = cudaMalloc(&b->spec, b->spec_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&b->dir_done, sizeof(unsigned) * lim->max_dirs);
   if (e == cudaSuccess) e = cudaMemset(b->dir_done, 0, sizeof(unsigned) * lim->max_dirs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dir_pre, sizeof(DirPre) * lim->max_dirs);
   for (int set = 0; set < 2 && e == cudaSuccess; ++set) e = cudaEventCreateWithFlags(&b->done[set], cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(fail(ctx, AR_ERR_OUT_OF_MEMORY, "batch allocation failed: %s", cudaGetErrorString(e)));
   for (int c = 0; c < kClasses; ++c) {
@@ -1363,6 +1372,7 @@ ar_status ar_batch_destroy(ar_batch* b) {
   }
   cudaFree(b->spec);
   cudaFree(b->dir_done);
+  cudaFree(b->dir_pre);
   delete b;
   return AR_OK;
 }

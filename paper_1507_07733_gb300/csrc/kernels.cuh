@@ -162,6 +162,8 @@ struct PatternRef {
   int n_zen, n_az, n_f, pad;
 };
 
+struct DirPre;
+
 // One event. A plain call passes it inline in the kernel parameters; a batch launch reads
 // an array of them, behind a header, from device memory (so a captured graph can be
 // replayed with new events after a copy into that memory).
@@ -183,6 +185,7 @@ struct EventDesc {
   double* chi2;            // [D]
   float4* spec;            // [S][M] station band spectra (library workspace)
   unsigned* dir_done;      // [D] pairs finished per direction (library workspace)
+  DirPre* dir_pre;         // [D] per-direction cells and vectors (library workspace), or null
   const float2* table;     // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
   const int2* binf;        // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
   const float2* t1;        // [4][Q][P] pass-1 output twiddles
@@ -314,6 +317,9 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ in, fl
   }
 }
 
+// the per-direction cells and source vectors of an event (whole CTA; defined with the cells)
+__device__ void precompute_directions(const EventDesc& ev, int tid, int nthreads);
+
 // One CTA per station of the launch. x[4m + r] (both channels packed as v0 + i v1) -> four
 // M-point DFTs U_r by three Stockham stages, then Z[k] = sum_r W_N^{kr} U_r[k mod M] at the
 // band bins and the split into the two channels' spectra.
@@ -360,8 +366,10 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
   const float2* U = x1;                                      // U_r[k'] at [r][k']
   // the previous kernel in the stream may still read these spectra: wait before writing them
   if (prm.wait_prior) pdl_wait_prior();
-  if (s == 0)
+  if (s == 0) {
     for (int d = tid; d < ev->n_dir; d += T) ev->dir_done[d] = 0u;
+    if (ev->dir_pre) precompute_directions(*ev, tid, T);
+  }
   if (ev->st_walk) {   // this station's position in the walk: stable by pattern, unknown ids last
     const int S = ev->n_st, np = ev->n_pats;
     const auto key = [&](int x) { const int p = station_pattern(*ev, x); return p < 0 ? np : p; };
@@ -413,6 +421,14 @@ struct DirInfo {
   float w[4];                       // bilinear weights of the corners
   unsigned st;
   int pat;                          // the station pattern the cell belongs to (station_pattern)
+};
+
+// Per direction of a launch, formed once by the station kernel: the direction cell in the
+// event's own pattern (events without station ids) and the unit vector toward the source.
+struct DirPre {
+  DirInfo cell;
+  double n[3];
+  double pad;
 };
 
 // Direction -> pattern cell (FP64, no fused multiply-adds) -> FP32 bilinear weights.
@@ -571,19 +587,29 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 template <int T>
 __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, double* red) {
   static_assert(T / 32 >= 3, "red holds the direction vector");
-  // the direction vector by one thread (FP64 is a small fraction of the FP32 rate), shared
-  // through red (at least 4 doubles; block_sum_fixed synchronises before reusing it)
-  if (threadIdx.x == 0) {
-    const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
-    double sz, cz, sa, ca;   // sincos: the same values as separate sin and cos, half the FP64 work
-    sincos(zen, &sz, &cz);
-    sincos(az, &sa, &ca);
-    red[0] = __dmul_rn(sz, ca);
-    red[1] = __dmul_rn(sz, sa);
-    red[2] = cz;
+  // the direction vector: precomputed by the station kernel, else by one thread here (FP64
+  // is a small fraction of the FP32 rate) and shared through red (at least 4 doubles;
+  // block_sum_fixed synchronises before reusing it)
+  double nx, ny, nz;
+  if (p.dir_pre) {
+    nx = __ldcg(&p.dir_pre[d].n[0]);
+    ny = __ldcg(&p.dir_pre[d].n[1]);
+    nz = __ldcg(&p.dir_pre[d].n[2]);
+  } else {
+    if (threadIdx.x == 0) {
+      const double zen = p.dirs[2 * d], az = p.dirs[2 * d + 1];
+      double sz, cz, sa, ca;   // sincos: the same values as separate sin and cos, half the FP64 work
+      sincos(zen, &sz, &cz);
+      sincos(az, &sa, &ca);
+      red[0] = __dmul_rn(sz, ca);
+      red[1] = __dmul_rn(sz, sa);
+      red[2] = cz;
+    }
+    __syncthreads();
+    nx = red[0];
+    ny = red[1];
+    nz = red[2];
   }
-  __syncthreads();
-  const double nx = red[0], ny = red[1], nz = red[2];
   const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
   // with SNRs the fit weights station s by w_s = snr (a variant; its timing variance taken
   // inversely proportional to the SNR): t0 = sum w d / sum w, chi2 = sum w r^2; unweighted
@@ -640,6 +666,41 @@ __device__ __forceinline__ DirInfo pair_cell(const EventDesc& ev, int d, int p, 
   return di;
 }
 
+__device__ void precompute_directions(const EventDesc& ev, int tid, int nthreads) {
+  for (int d = tid; d < ev.n_dir; d += nthreads) {
+    DirPre dp;
+    if (ev.st_pat) {
+      dp.cell = DirInfo{};
+    } else {
+      dp.cell = pair_cell(ev, d, -1, nullptr);
+    }
+    const double zen = ev.dirs[2 * d], az = ev.dirs[2 * d + 1];
+    double sz, cz, sa, ca;
+    sincos(zen, &sz, &cz);
+    sincos(az, &sa, &ca);
+    dp.n[0] = __dmul_rn(sz, ca);
+    dp.n[1] = __dmul_rn(sz, sa);
+    dp.n[2] = cz;
+    dp.pad = 0.0;
+    ev.dir_pre[d] = dp;
+  }
+}
+
+// The cell of direction d in the event's own pattern as the station kernel formed it (read
+// through L2: it was written by the previous kernel).
+__device__ __forceinline__ DirInfo load_cell(const DirPre* dp) {
+  DirInfo c;
+  c.slab0 = __ldcg(&dp->cell.slab0);
+  c.slab1 = __ldcg(&dp->cell.slab1);
+  c.slab2 = __ldcg(&dp->cell.slab2);
+  c.slab3 = __ldcg(&dp->cell.slab3);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c.w[i] = __ldcg(&dp->cell.w[i]);
+  c.st = __ldcg(&dp->cell.st);
+  c.pat = __ldcg(&dp->cell.pat);
+  return c;
+}
+
 // Whether a key's corner slabs are staged in shared memory by bulk copies (else read from
 // the L2-resident table when the key's inverse is built).
 __device__ __forceinline__ bool slab_staged(const EventDesc& ev, int p) { return p != -2 && !ev.slab_direct; }
@@ -647,10 +708,12 @@ __device__ __forceinline__ bool slab_staged(const EventDesc& ev, int p) { return
 // For a new (direction, pattern) key (thread 0 only): the key's direction cell into sdir and,
 // when the slabs are staged, the bulk copies of the pattern's four corner slabs, completing
 // the mbarrier's current phase.
+// With pre (after the wait for the station kernel) the event's own pattern's cell is taken
+// from the direction's precomputed entry instead of being formed here in FP64.
 __device__ __forceinline__ void issue_key(const EventDesc& ev, int d, int p, DirInfo* sdir, float2* slab,
-                                          uint64_t* bar) {
-  PatternRef pr;
-  const DirInfo di = pair_cell(ev, d, p, &pr);
+                                          uint64_t* bar, bool pre = false) {
+  const PatternRef pr = pattern_ref(ev, p);
+  const DirInfo di = (pre && p == -1 && ev.dir_pre) ? load_cell(ev.dir_pre + d) : pair_cell(ev, d, p, nullptr);
   *sdir = di;
   if (!slab_staged(ev, p)) return;
   const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
@@ -908,7 +971,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     const bool next_key = has_next && (dir_end || p_next != p);
     if (tid == 0 && next_key) {   // the next key's direction cell and corner slabs
       fence_proxy_async_smem();
-      issue_key(evn, d_next, p_next, sdir, slab, bar);
+      issue_key(evn, d_next, p_next, sdir, slab, bar, true);
     }
     pending = next_key && slab_staged(evn, p_next);
 
