@@ -610,7 +610,15 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
     ny = red[1];
     nz = red[2];
   }
-  const double* tp = (p.peak_fine ? p.peak_fine : p.peak_time) + static_cast<size_t>(d) * p.n_st;
+  // The stations' peak times t_start + index * dt (FP64) are formed here, the direction's
+  // stations in parallel, rather than by one thread per pair; with sub-sample times (formed
+  // per pair) the fit uses those.
+  const int* ip = p.peak_idx + static_cast<size_t>(d) * p.n_st;
+  double* ptime = p.peak_time + static_cast<size_t>(d) * p.n_st;
+  const double* fine = p.peak_fine ? p.peak_fine + static_cast<size_t>(d) * p.n_st : nullptr;
+  const auto time_of = [&](int s) {
+    return __dadd_rn(p.t_start[s], __dmul_rn(static_cast<double>(__ldcg(ip + s)), p.dt_ns));
+  };
   // with SNRs the fit weights station s by w_s = snr (a variant; its timing variance taken
   // inversely proportional to the SNR): t0 = sum w d / sum w, chi2 = sum w r^2; unweighted
   // when there are none or they sum to 0
@@ -619,7 +627,9 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   for (int s = threadIdx.x; s < p.n_st; s += T) {
     const double* x = p.pos + 3 * s;
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    const double ds = __dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c));   // t_s - tau_s
+    const double ts = time_of(s);
+    ptime[s] = ts;
+    const double ds = __dadd_rn(fine ? __ldcg(fine + s) : ts, __dmul_rn(dot, p.n_over_c));   // t_s - tau_s
     acc = __dadd_rn(acc, ds);
     if (wp) {
       const double w = static_cast<double>(__ldcg(wp + s));
@@ -640,7 +650,7 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   for (int s = threadIdx.x; s < p.n_st; s += T) {
     const double* x = p.pos + 3 * s;
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    const double r = __dsub_rn(__dadd_rn(__ldcg(tp + s), __dmul_rn(dot, p.n_over_c)), mean);
+    const double r = __dsub_rn(__dadd_rn(fine ? __ldcg(fine + s) : time_of(s), __dmul_rn(dot, p.n_over_c)), mean);
     res[s] = r;
     ss = weighted ? __fma_rn(__dmul_rn(static_cast<double>(__ldcg(wp + s)), r), r, ss) : __fma_rn(r, r, ss);
   }
@@ -1097,8 +1107,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       }
       if (bv < 0.f) { bv = 0.f; bi = 0; }
       ev.peak_idx[pair] = bi;
-      ev.peak_amp[pair] = bv;
-      ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+      ev.peak_amp[pair] = bv;   // the peak time is formed with the direction's residual
       if (ev.peak_fine)
         ev.peak_fine[pair] =
             __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(stage + 2 * N, N, bi)),
