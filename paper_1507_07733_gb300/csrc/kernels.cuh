@@ -144,6 +144,13 @@ __device__ __forceinline__ void tma_bulk_wait_all() { asm volatile("cp.async.bul
 
 // programmatic dependent launch: let the next kernel in the stream start its prologue, and
 // wait for the previous kernel's completion (both are no-ops without the launch attribute)
+// atomic add with acquire-release semantics at GPU scope; returns the previous value
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -1115,10 +1122,11 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
       if (want_snr) ev.snr[pair] = snr;
       if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
-        __threadfence();
-        const unsigned before = atomicAdd(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
+        // one acquire-release add: it releases this thread's outputs of the direction (the
+        // only ones the residual reads) and acquires every other CTA's; the barrier below
+        // passes them on to the CTA's other threads
+        const unsigned before = atom_add_acq_rel(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
         *sflag = (before + pairs_in_dir == static_cast<unsigned>(S)) ? 1 : 0;
-        __threadfence();
       }
     }
     if (dir_end) {
