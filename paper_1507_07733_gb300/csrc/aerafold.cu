@@ -445,6 +445,7 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
   d.daz = pd.daz_rad;
   d.dt_ns = 1e9 / ev->fs_hz;
   d.n_over_c = (ev->refractive_index > 0.0 ? ev->refractive_index : 1.0) / kCMPerNs;
+  d.inv_n_st = 1.0 / static_cast<double>(ev->n_stations);
   d.pair_begin = 0;
   d.station_begin = 0;
   d.n_zen = pd.n_zen;

@@ -201,6 +201,7 @@ struct EventDesc {
   const int* st_pat;       // [S] pattern id per station, or null: every station uses the fields here
   int2* st_walk;           // [S] with st_pat: (station, pattern index) in walk order, written by the station kernel
   double zen0, dzen, az0, daz, dt_ns, n_over_c;
+  double inv_n_st;         // 1 / n_st (FP64, from the host): the fit's mean as a product
   long long pair_begin;    // first pair of the event in the launch's flattened pair space
   int station_begin;       // first station of the event in the launch's flattened station space
   int n_zen, n_az, n_f, n_st, n_dir, k_lo;
@@ -631,12 +632,14 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
   // when there are none or they sum to 0
   const float* wp = p.snr ? p.snr + static_cast<size_t>(d) * p.n_st : nullptr;
   double acc = 0.0, accw = 0.0, accwd = 0.0;
+  double ds0 = 0.0;   // t_s - tau_s of this thread's first station, kept for the second pass
   for (int s = threadIdx.x; s < p.n_st; s += T) {
     const double* x = p.pos + 3 * s;
     const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
     const double ts = time_of(s);
     ptime[s] = ts;
     const double ds = __dadd_rn(fine ? __ldcg(fine + s) : ts, __dmul_rn(dot, p.n_over_c));   // t_s - tau_s
+    if (s == threadIdx.x) ds0 = ds;
     acc = __dadd_rn(acc, ds);
     if (wp) {
       const double w = static_cast<double>(__ldcg(wp + s));
@@ -651,13 +654,17 @@ __device__ __forceinline__ void direction_residual(const EventDesc& p, int d, do
     swd = block_sum_fixed<T>(accwd, red);
   }
   const bool weighted = wp && sw > 0.0;
-  const double mean = weighted ? __ddiv_rn(swd, sw) : __ddiv_rn(sum, static_cast<double>(p.n_st));
+  const double mean = weighted ? __ddiv_rn(swd, sw) : __dmul_rn(sum, p.inv_n_st);
   double ss = 0.0;
   double* res = p.residual + static_cast<size_t>(d) * p.n_st;
   for (int s = threadIdx.x; s < p.n_st; s += T) {
-    const double* x = p.pos + 3 * s;
-    const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
-    const double r = __dsub_rn(__dadd_rn(fine ? __ldcg(fine + s) : time_of(s), __dmul_rn(dot, p.n_over_c)), mean);
+    double ds = ds0;
+    if (s != threadIdx.x) {
+      const double* x = p.pos + 3 * s;
+      const double dot = __dadd_rn(__dadd_rn(__dmul_rn(nx, x[0]), __dmul_rn(ny, x[1])), __dmul_rn(nz, x[2]));
+      ds = __dadd_rn(fine ? __ldcg(fine + s) : time_of(s), __dmul_rn(dot, p.n_over_c));
+    }
+    const double r = __dsub_rn(ds, mean);
     res[s] = r;
     ss = weighted ? __fma_rn(__dmul_rn(static_cast<double>(__ldcg(wp + s)), r), r, ss) : __fma_rn(r, r, ss);
   }
