@@ -475,7 +475,7 @@ cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cuda
   pp.ev0 = desc;
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
-  station_spectrum_kernel<N_><<<desc.n_st, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream>>>(pp);
+  station_spectrum_kernel<N_><<<desc.n_st, SpectrumSmem<N_>::BLOCK, SpectrumSmem<N_>::TOTAL, stream>>>(pp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (evs && (e = cudaEventRecord(evs[1], stream)) != cudaSuccess) return e;
   const long long pairs = static_cast<long long>(desc.n_st) * desc.n_dir;
@@ -699,7 +699,7 @@ cudaError_t launch_recon(ar_ctx* ctx, const ar_event* ev, int max_iter, double t
   // the station spectra, once: every iteration unfolds the same traces
   PathParams sp = pp;
   sp.skip = nullptr;
-  station_spectrum_kernel<N_><<<S, SpectrumSmem<N_>::THREADS, SpectrumSmem<N_>::TOTAL, stream>>>(sp);
+  station_spectrum_kernel<N_><<<S, SpectrumSmem<N_>::BLOCK, SpectrumSmem<N_>::TOTAL, stream>>>(sp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   voltage_peak_kernel<<<S, 256, 0, stream>>>(ev->traces, ev->t_start_ns, ev->n_samples, dt_ns, vidx, vtimes);
   FitParams fp{ev->pos_m, vtimes, vidx, prev_idx, st, out->history, n_over_c, tol_rad, S, 0};
@@ -1189,7 +1189,7 @@ template <int N_>
 cudaError_t batch_station_launch(ar_batch* b, int c, cudaStream_t st) {
   using L = Layout<N_>;
   return launch_pdl(station_spectrum_kernel<N_>, std::min(b->lim.max_stations, 4 * b->ctx->num_sms),
-                    SpectrumSmem<N_>::THREADS,
+                    SpectrumSmem<N_>::BLOCK,
                     SpectrumSmem<N_>::TOTAL, st, batch_params<N_>(b, c, 1));
 }
 

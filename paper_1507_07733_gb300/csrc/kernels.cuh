@@ -296,7 +296,8 @@ struct StationRadix<4096> { static constexpr int R0 = 16, R1 = 8, R2 = 8; };
 template <int N_>
 struct SpectrumSmem {
   static constexpr int N = N_, M = N_ / 4;
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = 256;                              // the transform's threads
+  static constexpr int BLOCK = THREADS + 32;                       // and one warp for the direction entries
   static constexpr size_t X0 = 0;                                  // [4][M] float2 (ping)
   static constexpr size_t X1 = X0 + sizeof(float2) * 4 * M;        // [4][M] float2 (pong)
   static constexpr size_t TW = X1 + sizeof(float2) * 4 * M;        // [M] exp(-2 pi i x / M)
@@ -325,14 +326,14 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ in, fl
   }
 }
 
-// the per-direction cells and source vectors of an event (whole CTA; defined with the cells)
-__device__ void precompute_directions(const EventDesc& ev, int tid, int nthreads);
+// a part of direction d's per-direction entry (defined with the cells)
+__device__ void precompute_direction(const EventDesc& ev, int d, int part, bool valid);
 
 // One CTA per station of the launch. x[4m + r] (both channels packed as v0 + i v1) -> four
 // M-point DFTs U_r by three Stockham stages, then Z[k] = sum_r W_N^{kr} U_r[k mod M] at the
 // band bins and the split into the two channels' spectra.
 template <int N_>
-__global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_kernel(const __grid_constant__ PathParams prm) {
+__global__ void __launch_bounds__(SpectrumSmem<N_>::BLOCK) station_spectrum_kernel(const __grid_constant__ PathParams prm) {
   using SM = SpectrumSmem<N_>;
   using RD = StationRadix<N_>;
   constexpr int N = N_, M = SM::M, T = SM::THREADS;
@@ -343,6 +344,9 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
   float2* tw = reinterpret_cast<float2*>(smem_raw + SM::TW);
   const int tid = threadIdx.x;
   pdl_launch_dependents();
+  // threads [0, T) transform (their barriers are named barrier 1); the last warp forms the
+  // per-direction entries meanwhile (directions s, s + S, ... of the event for station s)
+  const auto sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(SM::THREADS) : "memory"); };
   // a plain launch has one CTA per station; a batch launch walks the stations grid-stride
   const int total = prm.batch ? prm.batch->total_stations : prm.ev0.n_st;
   for (int gs = blockIdx.x; gs < total; gs += gridDim.x) {
@@ -352,6 +356,20 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
     ev = evs + find_event(prm.batch->n_events, gs, [&](int e) { return static_cast<long long>(evs[e].station_begin); });
   }
   const int s = gs - ev->station_begin;
+  if (tid >= T) {
+    if (ev->dir_pre) {
+      // the previous kernel in the stream may still read the entries: wait before writing.
+      // Ten direction slots of three lanes (see precompute_direction); lanes 30, 31 idle.
+      if (prm.wait_prior) pdl_wait_prior();
+      const int lane = tid - T, slot = lane / 3, part = lane % 3;
+      const int S = ev->n_st, D = ev->n_dir;
+      for (int base = s; base < D; base += 10 * S) {   // warp-uniform trip count
+        const int d = base + S * slot;
+        precompute_direction(*ev, d, part, slot < 10 && d < D);
+      }
+    }
+    continue;
+  }
 
   const float4* v0 = reinterpret_cast<const float4*>(ev->traces + static_cast<size_t>(s) * 2 * N);
   const float4* v1 = v0 + N / 4;
@@ -364,20 +382,18 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
     x0[3 * M + m] = make_float2(a.w, b.w);
     tw[m] = __ldg(wn + 4 * m);                               // exp(-2 pi i m / M)
   }
-  __syncthreads();
+  sync();
   stockham_stage<M, RD::R0>(x0, x1, tw, 1, tid, T);
-  __syncthreads();
+  sync();
   stockham_stage<M, RD::R1>(x1, x0, tw, RD::R0, tid, T);
-  __syncthreads();
+  sync();
   stockham_stage<M, RD::R2>(x0, x1, tw, RD::R0 * RD::R1, tid, T);
-  __syncthreads();
+  sync();
   const float2* U = x1;                                      // U_r[k'] at [r][k']
   // the previous kernel in the stream may still read these spectra: wait before writing them
   if (prm.wait_prior) pdl_wait_prior();
-  if (s == 0) {
+  if (s == 0)
     for (int d = tid; d < ev->n_dir; d += T) ev->dir_done[d] = 0u;
-    if (ev->dir_pre) precompute_directions(*ev, tid, T);
-  }
   if (ev->st_walk) {   // this station's position in the walk: stable by pattern, unknown ids last
     const int S = ev->n_st, np = ev->n_pats;
     const auto key = [&](int x) { const int p = station_pattern(*ev, x); return p < 0 ? np : p; };
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
     for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
     int* part = reinterpret_cast<int*>(x0);   // free since the last Stockham stage
     if ((tid & 31) == 0) part[tid >> 5] = c;
-    __syncthreads();
+    sync();
     if (tid == 0) {
       int rank = 0;
 #pragma unroll
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::THREADS) station_spectrum_ke
     const float2 dif = make_float2(z.x - zm.x, z.y + zm.y);   // Z[k] - conj Z[N-k]
     out[j] = make_float4(0.5f * sum.x, 0.5f * sum.y, 0.5f * dif.y, -0.5f * dif.x);
   }
-  __syncthreads();   // shared buffers free for the next station
+  sync();   // shared buffers free for the next station
   }
 }
 
@@ -690,23 +706,26 @@ __device__ __forceinline__ DirInfo pair_cell(const EventDesc& ev, int d, int p, 
   return di;
 }
 
-__device__ void precompute_directions(const EventDesc& ev, int tid, int nthreads) {
-  for (int d = tid; d < ev.n_dir; d += nthreads) {
-    DirPre dp;
-    if (ev.st_pat) {
-      dp.cell = DirInfo{};
-    } else {
-      dp.cell = pair_cell(ev, d, -1, nullptr);
-    }
-    const double zen = ev.dirs[2 * d], az = ev.dirs[2 * d + 1];
-    double sz, cz, sa, ca;
-    sincos(zen, &sz, &cz);
-    sincos(az, &sa, &ca);
-    dp.n[0] = __dmul_rn(sz, ca);
-    dp.n[1] = __dmul_rn(sz, sa);
-    dp.n[2] = cz;
-    dp.pad = 0.0;
-    ev.dir_pre[d] = dp;
+// Part `part` (0, 1, 2) of direction d's entry, by three lanes of one warp in parallel (each
+// part is a chain of slow FP64 operations): 0 the cell, 1 and 2 the sine and cosine of the
+// zenith and of the azimuth, combined into the source vector by lane part 1. valid: d is a
+// direction of the event (all three lanes of a slot agree); the shuffles run regardless.
+__device__ void precompute_direction(const EventDesc& ev, int d, int part, bool valid) {
+  double sv = 0.0, cv = 0.0;
+  if (valid && part == 0) {
+    DirPre* dp = ev.dir_pre + d;
+    dp->cell = ev.st_pat ? DirInfo{} : pair_cell(ev, d, -1, nullptr);
+  } else if (valid) {
+    sincos(ev.dirs[2 * d + (part - 1)], &sv, &cv);
+  }
+  // part 1 (zenith) takes the azimuth's sine and cosine from part 2, the next lane
+  const double sa = __shfl_down_sync(0xffffffffu, sv, 1), ca = __shfl_down_sync(0xffffffffu, cv, 1);
+  if (valid && part == 1) {
+    DirPre* dp = ev.dir_pre + d;
+    dp->n[0] = __dmul_rn(sv, ca);
+    dp->n[1] = __dmul_rn(sv, sa);
+    dp->n[2] = cv;
+    dp->pad = 0.0;
   }
 }
 
