@@ -526,8 +526,7 @@ __global__ void __launch_bounds__(kSub) tc_inverse_post_kernel(const __grid_cons
     pk_v = bv;
     pk_i = bi;
     ev.peak_idx[pair] = bi;
-    ev.peak_amp[pair] = bv;
-    ev.peak_time[pair] = __dadd_rn(ev.t_start[s], __dmul_rn(static_cast<double>(bi), ev.dt_ns));
+    ev.peak_amp[pair] = bv;   // the peak time is formed with the direction's residual
     if (ev.peak_fine)
       ev.peak_fine[pair] =
           __dadd_rn(ev.t_start[s], __dmul_rn(__dadd_rn(static_cast<double>(bi), peak_offset(senv, N, bi)), ev.dt_ns));
