@@ -375,8 +375,8 @@ def run_single_event(binding, synth, ctx, pid, dev, stream, reps=200):
     import torch
     ev = synth.single_event(2048)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    e = binding.make_event(pid, t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad), ev.fs_hz)
-    keep = e
+    keep = (t(ev.traces), t(ev.pos_m), t(ev.t_start_ns), t(ev.dirs_rad))   # the event holds raw pointers
+    e = binding.make_event(pid, *keep, ev.fs_hz)
     o, ost = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device=dev)
     sp = stream.cuda_stream
     for _ in range(20):
@@ -397,7 +397,8 @@ def run_single_event(binding, synth, ctx, pid, dev, stream, reps=200):
         binding.ar_sync(ctx.h, sp)
         host_us.append((time.perf_counter() - t0) * 1e6)
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-    he = binding.make_event(pid, pin(ev.traces), pin(ev.pos_m), pin(ev.t_start_ns), pin(ev.dirs_rad), ev.fs_hz)
+    hkeep = (pin(ev.traces), pin(ev.pos_m), pin(ev.t_start_ns), pin(ev.dirs_rad))
+    he = binding.make_event(pid, *hkeep, ev.fs_hz)
     ho, host_o = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples, device="cpu", pin_memory=True)
     e2e_us = []
     for _ in range(reps):

@@ -63,7 +63,9 @@ typedef enum ar_status {
 /* per-pair status bits (ar_outputs.status) */
 #define AR_STATUS_SINGULAR 1u    /* at least one in-band bin was near-singular (E set to 0) */
 #define AR_STATUS_ZEN_CLAMP 2u   /* the zenith lay outside the table and was clamped        */
-#define AR_STATUS_BAD_DIR 4u     /* the direction was not finite: every output of the pair is 0 */
+#define AR_STATUS_BAD_DIR 4u     /* the direction was not finite, or its azimuth 2^52 or more
+                                    azimuth steps from the pattern's az0: every output of the
+                                    pair is 0 */
 #define AR_STATUS_BAD_PATTERN 8u /* station_pattern named no loaded pattern: every output is 0 */
 
 typedef struct ar_ctx ar_ctx;

@@ -43,7 +43,7 @@
 
 #define ORC_ST_SINGULAR 1u     /* at least one in-band bin had a near-singular H */
 #define ORC_ST_ZEN_CLAMP 2u    /* zenith outside the table, clamped to its edge */
-#define ORC_ST_BAD_DIR 4u      /* non-finite direction: all outputs zero */
+#define ORC_ST_BAD_DIR 4u      /* direction without a cell (see orc_dir_ok): all outputs zero */
 
 typedef struct {
   int32_t n_zen;  double zen0_rad, dzen_rad;
@@ -176,6 +176,14 @@ int orc_solve(const double *H, const double *V /* [2][re,im] */, double *E /* [2
 
 /* ---- 4.-6. one (station, direction) pair from the station's spectra ------------------ */
 
+/* A direction the pattern can be evaluated at: finite, with an azimuth less than 2^52
+ * azimuth steps from az0 (beyond, one FP64 unit is a whole step and the position inside the
+ * period is lost). Any other direction has no cell and is treated like a non-finite one. */
+static int orc_dir_ok(const orc_pattern *pt, double zen, double az) {
+  if (!isfinite(zen) || !isfinite(az)) return 0;
+  return fabs((az - pt->az0_rad) / pt->daz_rad) < 0x1p52;
+}
+
 /* Unfold one pair. spec = orc_station_spectrum output. Writes efield [2][N] (may be NULL),
  * env [N] (may be NULL), the peak index/amplitude and the status bits. min_margin gets the
  * smallest |det|/scale over in-band bins (used by tests to skip bins near the threshold). */
@@ -188,7 +196,7 @@ void orc_unfold_pair(const orc_pattern *pt, const float *table, int n, double fs
   double *Z = (double *)calloc((size_t)4 * n, sizeof(double));   /* [2 pol][N][2] */
   double *z = (double *)malloc(sizeof(double) * 4 * (size_t)n);
   double *e = (double *)malloc(sizeof(double) * 3 * (size_t)n);  /* e_t, e_p, env */
-  if (!isfinite(zen) || !isfinite(az)) {
+  if (!orc_dir_ok(pt, zen, az)) {
     st |= ORC_ST_BAD_DIR;
     memset(e, 0, sizeof(double) * 3 * (size_t)n);
   } else {

@@ -23,6 +23,8 @@ AR_OK = 0
 STATUS_NAMES = ["AR_OK", "AR_ERR_INVALID_ARG", "AR_ERR_UNSUPPORTED_N", "AR_ERR_NO_PATTERN",
                 "AR_ERR_OUT_OF_MEMORY", "AR_ERR_BUDGET", "AR_ERR_CUDA", "AR_ERR_TIMEOUT",
                 "AR_ERR_NOT_READY", "AR_ERR_DEVICE"]
+AR_ERR_TIMEOUT = STATUS_NAMES.index("AR_ERR_TIMEOUT")
+AR_ERR_NOT_READY = STATUS_NAMES.index("AR_ERR_NOT_READY")
 AR_STATUS_SINGULAR = 1
 AR_STATUS_ZEN_CLAMP = 2
 AR_STATUS_BAD_DIR = 4
@@ -298,14 +300,17 @@ def _ptr(t):
 def make_event(pattern_id: int, traces, pos_m, t_start_ns, dirs_rad, fs_hz: float = 200e6,
                refractive_index: float = 1.0, station_pattern=None) -> ar_event:
     """Build an ``ar_event`` from tensors (device or host, matching the call used);
-    ``station_pattern`` is an optional int32 tensor of pattern ids, one per station."""
+    ``station_pattern`` is an optional int32 tensor of pattern ids, one per station. The
+    struct keeps references to the tensors, so they live at least as long as it does."""
     S, two, N = traces.shape
     assert two == 2
     if station_pattern is not None:
         assert station_pattern.dtype.itemsize == 4 and station_pattern.numel() == S
-    return ar_event(S, N, dirs_rad.shape[0], pattern_id, fs_hz, refractive_index,
-                    _ptr(traces), _ptr(pos_m), _ptr(t_start_ns), _ptr(dirs_rad),
-                    _ptr(station_pattern) if station_pattern is not None else None)
+    ev = ar_event(S, N, dirs_rad.shape[0], pattern_id, fs_hz, refractive_index,
+                  _ptr(traces), _ptr(pos_m), _ptr(t_start_ns), _ptr(dirs_rad),
+                  _ptr(station_pattern) if station_pattern is not None else None)
+    ev._tensors = (traces, pos_m, t_start_ns, dirs_rad, station_pattern)
+    return ev
 
 
 def alloc_outputs(n_dirs: int, n_stations: int, n_samples: int, device="cuda", traces: bool = True,
@@ -484,26 +489,38 @@ class Server:
         self.ctx = ctx
         self.h = ar_server_create(ctx.h, state_budget_bytes, max_batch_events, max_inflight, max_stations_per_event,
                                   max_n_freq)
+        self._live = {}   # ticket -> (event, outputs): their memory must outlive the request
 
     def submit(self, ev: ar_event, out) -> int:
-        return ar_submit(self.ctx.h, self.h, ev, out if isinstance(out, ar_outputs) else outputs_struct(out))
+        t = ar_submit(self.ctx.h, self.h, ev, out if isinstance(out, ar_outputs) else outputs_struct(out))
+        self._live[t] = (ev, out)
+        return t
+
+    def _settled(self, ticket: int, st: int) -> int:
+        if st not in (AR_ERR_NOT_READY, AR_ERR_TIMEOUT):
+            self._live.pop(ticket, None)
+        return st
 
     def poll(self, ticket: int) -> int:
-        return ar_poll(self.h, ticket)
+        return self._settled(ticket, ar_poll(self.h, ticket))
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
-        return ar_wait(self.h, ticket, timeout_ms)
+        return self._settled(ticket, ar_wait(self.h, ticket, timeout_ms))
 
     def times(self, ticket: int):
         return ar_ticket_times(self.h, ticket)
 
     def release(self, ticket: int) -> int:
-        return ar_ticket_release(self.h, ticket)
+        st = ar_ticket_release(self.h, ticket)
+        if st == AR_OK:
+            self._live.pop(ticket, None)
+        return st
 
     def close(self):
         if self.h:
-            ar_server_destroy(self.h)
+            ar_server_destroy(self.h)   # finishes every queued and running request
             self.h = None
+            self._live.clear()
 
     def __del__(self):
         try:

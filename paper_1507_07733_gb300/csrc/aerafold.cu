@@ -138,26 +138,22 @@ float2 unit(long t, long n, int sign) {   // exp(sign * 2 pi i t / n), t reduced
   return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(sign * std::sin(a)));
 }
 
-// the pass-1 pre-twiddles exp(2 pi i jb r / 4Q) into the kernels' constant tables (current device)
-cudaError_t upload_pretwiddles() {
-  float2 a[4][32], b[4][16];
-  for (int r = 0; r < 4; ++r) {
-    for (int j = 0; j < 32; ++j) a[r][j] = unit(static_cast<long>(j) * r, 128, +1);
-    for (int j = 0; j < 16; ++j) b[r][j] = unit(static_cast<long>(j) * r, 64, +1);
-  }
-  cudaError_t e = cudaMemcpyToSymbol(c_pre32, a, sizeof a);
-  return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_pre16, b, sizeof b);
-}
-
 template <int N_>
 ar_status build_len_tables(ar_ctx* ctx, int k_lo, LenTables* lt) {
   using L = Layout<N_>;
   constexpr int N = L::N, Q = L::Q, P = L::P;
-  std::vector<float2> t1(4 * Q * P), wn(N);
+  std::vector<float2> t1(4 * Q * P + (L::SPLIT == 1 ? 8 * Q : 0)), wn(N);
   for (int r = 0; r < 4; ++r)
     for (int mb = 0; mb < Q; ++mb)
       for (int ja = 0; ja < P; ++ja)
         t1[(r * Q + mb) * P + ja] = unit(static_cast<long>(k_lo + ja) * (r + 4 * mb), N, +1);
+  if (L::SPLIT == 1) {   // pass 2's c = exp(2 pi i P floor(k_lo/P) w / N) and u = exp(2 pi i w / N), w = 4 mb + r
+    const long base = static_cast<long>(k_lo / P) * P;
+    for (int w = 0; w < 4 * Q; ++w) {
+      t1[4 * Q * P + w] = unit(base * w, N, +1);
+      t1[4 * Q * P + 4 * Q + w] = unit(w, N, +1);
+    }
+  }
   for (int t = 0; t < N; ++t) wn[t] = unit(t, N, -1);
   AR_CUDA(ctx, cudaMalloc(&lt->t1, t1.size() * sizeof(float2)));
   AR_CUDA(ctx, cudaMalloc(&lt->wn, wn.size() * sizeof(float2)));
@@ -570,7 +566,7 @@ ar_status ar_create(ar_ctx** out, const ar_config* cfg) {
   ctx->cfg = c;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess || upload_pretwiddles() != cudaSuccess) {
+      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
     delete ctx;
     return create_fail(AR_ERR_OUT_OF_MEMORY, "context allocation failed");
   }
@@ -1953,20 +1949,27 @@ __global__ void noalloc_tables_kernel(float2* t1, float2* wn, int2* binf, int k_
                                       int n_f) {
   using L = Layout<N_>;
   constexpr int N = L::N, M = L::M, Q = L::Q, P = L::P;
-  const int total = 4 * Q * P + N + M;
+  constexpr int NT1 = 4 * Q * P + (L::SPLIT == 1 ? 8 * Q : 0);   // pass-1 twiddles, then pass 2's (c, u)
+  const int total = NT1 + N + M;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     double s, c;
-    if (i < 4 * Q * P) {
-      const int r = i / (Q * P), mb = (i / P) % Q, ja = i % P;
-      const long t = (static_cast<long>(k_lo + ja) * (r + 4 * mb)) % N;
+    if (i < NT1) {
+      long t;
+      if (i < 4 * Q * P) {
+        const int r = i / (Q * P), mb = (i / P) % Q, ja = i % P;
+        t = (static_cast<long>(k_lo + ja) * (r + 4 * mb)) % N;
+      } else {
+        const int w = (i - 4 * Q * P) % (4 * Q);
+        t = i - 4 * Q * P < 4 * Q ? (static_cast<long>(k_lo / P) * P * w) % N : w;
+      }
       sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
       t1[i] = make_float2(static_cast<float>(c), static_cast<float>(s));
-    } else if (i < 4 * Q * P + N) {
-      const int t = i - 4 * Q * P;
+    } else if (i < NT1 + N) {
+      const int t = i - NT1;
       sincospi(2.0 * static_cast<double>(t) / N, &s, &c);
       wn[t] = make_float2(static_cast<float>(c), static_cast<float>(-s));
     } else {
-      const int j = i - 4 * Q * P - N, k = k_lo + j;
+      const int j = i - NT1 - N, k = k_lo + j;
       const double f = __ddiv_rn(__dmul_rn(static_cast<double>(k), fs), static_cast<double>(N));
       if (!(f >= kBandLoHz && f <= kBandHiHz)) {
         binf[j] = make_int2(-1, 0);
@@ -1990,7 +1993,6 @@ ar_status noalloc_setup(int dev, NoAllocDevice** out) {
   if (!d.ready) {
     void* p = nullptr;
     AR_NA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    AR_NA_CUDA(upload_pretwiddles());
     AR_NA_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t sp1 = SpectrumSmem<1024>::TOTAL;
     const size_t sp2 = SpectrumSmem<2048>::TOTAL;
@@ -2017,6 +2019,7 @@ ar_status noalloc_launch(NoAllocDevice& nd, const ar_pattern_desc* pd, const flo
   b.err = reinterpret_cast<unsigned*>(base);
   b.dir_done = reinterpret_cast<unsigned*>(base + 256);                       // 16 KiB
   float2* t1 = reinterpret_cast<float2*>(base + 256 + (16u << 10));           // 32 KiB
+  static_assert(sizeof(float2) * (4 * L::Q * L::P + (L::SPLIT == 1 ? 8 * L::Q : 0)) <= (32u << 10), "T1 area");
   float2* wn = reinterpret_cast<float2*>(base + 256 + (48u << 10));           // 32 KiB
   int2* binf = reinterpret_cast<int2*>(base + 256 + (80u << 10));             // 8 KiB
   b.t1 = t1;

@@ -195,7 +195,7 @@ struct EventDesc {
   DirPre* dir_pre;         // [D] per-direction cells and vectors (library workspace), or null
   const float2* table;     // [n_zen][n_az][n_f][4] VEL (c0p0, c0p1, c1p0, c1p1)
   const int2* binf;        // [M]: (.x = frequency cell or -1 outside the band, .y = bits of t_f)
-  const float2* t1;        // [4][Q][P] pass-1 output twiddles
+  const float2* t1;        // [4][Q][P] pass-1 output twiddles; with SPLIT == 1 then [2][4Q] (c, u) of pass 2
   const float2* wn;        // [N] exp(-2 pi i t / N)
   const PatternRef* pats;  // with st_pat: the loaded patterns at this (N, fs), by pattern id
   const int* st_pat;       // [S] pattern id per station, or null: every station uses the fields here
@@ -460,7 +460,20 @@ __device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double ze
   DirInfo di;
   di.st = 0;
   di.pat = -1;
-  if (!isfinite(zen) || !isfinite(az)) {
+  // A direction has a cell when it is finite and its azimuth lies less than 2^52 azimuth
+  // steps from az0 (beyond, one FP64 unit is a whole step). Below that bound the remainder
+  // modulo n_az lands in [0, n_az]; the range test keeps every slab index in bounds.
+  double ua = 0.0;
+  bool has_cell = isfinite(zen) && isfinite(az);
+  if (has_cell) {
+    ua = __ddiv_rn(__dsub_rn(az, p.az0), p.daz);
+    has_cell = fabs(ua) < 0x1p52;
+  }
+  if (has_cell) {
+    ua = __dsub_rn(ua, __dmul_rn(double(p.n_az), floor(__ddiv_rn(ua, double(p.n_az)))));
+    has_cell = ua >= 0.0 && ua <= double(p.n_az);
+  }
+  if (!has_cell) {   // every output of the direction's pairs is 0
     di.st = kStBadDir;
     di.slab0 = di.slab1 = di.slab2 = di.slab3 = 0;
     di.w[0] = di.w[1] = di.w[2] = di.w[3] = 0.f;
@@ -472,8 +485,6 @@ __device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double ze
   int iz = static_cast<int>(floor(uz));
   if (iz > p.n_zen - 2) iz = p.n_zen - 2;
   const double tz = __dsub_rn(uz, double(iz));
-  double ua = __ddiv_rn(__dsub_rn(az, p.az0), p.daz);
-  ua = __dsub_rn(ua, __dmul_rn(double(p.n_az), floor(__ddiv_rn(ua, double(p.n_az)))));
   int ia = static_cast<int>(floor(ua));
   const double ta = __dsub_rn(ua, double(ia));
   if (ia >= p.n_az) ia -= p.n_az;
@@ -493,30 +504,79 @@ __device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double ze
 // Pre-twiddles of pass 1, exp(2 pi i jb r / 4Q) at [r][jb], for Q = 32 and Q = 16. They are
 // read with a warp-uniform r so that one copy of the pass-1 code serves all four r: the
 // kernel is limited by instruction fetch when the four variants are compiled separately.
-__constant__ float2 c_pre32[4][32];
-__constant__ float2 c_pre16[4][16];
+// pass-1 load with pre-twiddle: x[jb] = E_p[ja + P jb] exp(2 pi i jb R / 4Q) for one residue R,
+// the twiddles compile-time constants
+template <int Q, int P, int R>
+__device__ __forceinline__ void load_pre_twiddled(const float2* Ep, int ja, float2 (&x)[Q]) {
+  static_for<0, Q>([&](auto jb) {
+    constexpr long JB = decltype(jb)::value;
+    x[JB] = twmul<JB * R, 4 * Q, +1>(Ep[ja + P * JB]);
+  });
+}
+
+// The same with the output twiddle's band wrap absorbed: for sh = 1 the task's rows carry an
+// extra factor exp(2 pi i (4 mb + r) / 4Q) = exp(2 pi i mb / Q) exp(2 pi i r / 4Q), a cyclic
+// shift of the DFT input by one slot: slot jb reads E_p[ja + P (jb - 1)] with the slot's own
+// pre-twiddle, and slot 0 reads E_p[ja + P (Q - 1)] turned by i^R.
+template <int Q, int P, int R>
+__device__ __forceinline__ void load_pre_twiddled_wrap(const float2* Ep, int ja, bool sh, float2 (&x)[Q]) {
+  const int b = sh ? ja - P : ja;   // slot jb >= 1 reads b + P jb (always in [0, P Q))
+  const float2 e0 = Ep[sh ? ja + P * (Q - 1) : ja];
+  if constexpr (R == 0) {
+    x[0] = e0;
+  } else {
+    const float2 t = twmul<R, 4, +1>(e0);
+    x[0] = sh ? t : e0;
+  }
+  static_for<1, Q>([&](auto jb) {
+    constexpr long JB = decltype(jb)::value;
+    x[JB] = twmul<JB * R, 4 * Q, +1>(Ep[b + P * JB]);
+  });
+}
 
 // Pass 1 for one (pol, r, ja): load E_p[ja + P jb], pre-twiddle, Q-point inverse DFT, output
 // twiddle T1[r][mb][ja] = w0 v^mb with w0 = T1[r][0][ja], v = T1[0][1][ja] = exp(2 pi i (k_lo+ja) 4/N).
 // The twiddles are formed in registers as w0 (v^4)^i v^j (mb = 4i + j): two table loads per
 // task instead of Q, at most ten roundings deep (relative error ~1e-6, inside the path's 1e-5).
+//
+// With SPLIT == 1 each pass-2 thread holds both polarisations of one (r, mb), so the output
+// twiddle moves there and is formed once for both: write k_lo + ja = P (f0 + sh) + i with
+// i = (k_lo + ja) mod P the task's row and f0 = floor(k_lo / P). Then
+//   T1[r][mb][ja] = exp(2 pi i (P f0 + i)(4 mb + r) / N) * [sh] exp(2 pi i (4 mb + r) / 4Q);
+// the first factor depends on (r, mb, i) only and is applied in pass 2 (tau_i = c u^i with
+// c = exp(2 pi i P f0 (4 mb + r) / N), u = exp(2 pi i (4 mb + r) / N)), the second is the
+// one-slot input shift of load_pre_twiddled_wrap.
 template <int N_>
-__device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, const float2* __restrict__ t1,
+__device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, int k_lo, const float2* __restrict__ t1,
                                            float2 (&x)[Layout<N_>::Q]) {
   using L = Layout<N_>;
   constexpr int Q = L::Q, P = L::P;
-  static_assert(Q == 32 || Q == 16, "pre-twiddle tables exist for Q = 16 and 32");
-  const float2 w0 = __ldg(t1 + (r * Q) * P + ja);   // issued early: used after the DFT
-  const float2 v1 = __ldg(t1 + P + ja);
-  static_for<0, Q>([&](auto jb) {
-    constexpr int JB = decltype(jb)::value;
-    const float2 e = Ep[ja + P * JB];
-    if constexpr (JB == 0) {
-      x[JB] = e;
-    } else {
-      x[JB] = cmul(e, Q == 32 ? c_pre32[r][JB] : c_pre16[r][JB]);
+  if constexpr (L::SPLIT == 1) {
+    const bool sh = ja + k_lo % P >= P;
+    switch (r) {   // warp-uniform
+      case 0: load_pre_twiddled_wrap<Q, P, 0>(Ep, ja, sh, x); break;
+      case 1: load_pre_twiddled_wrap<Q, P, 1>(Ep, ja, sh, x); break;
+      case 2: load_pre_twiddled_wrap<Q, P, 2>(Ep, ja, sh, x); break;
+      default: load_pre_twiddled_wrap<Q, P, 3>(Ep, ja, sh, x); break;
     }
-  });
+    dft<Q, +1>(x);
+    return;
+  }
+  float2 w0, v1;   // issued early (used after the DFT) where the registers allow
+  if constexpr (P < 32) {
+    w0 = __ldg(t1 + (r * Q) * P + ja);
+    v1 = __ldg(t1 + P + ja);
+  }
+  switch (r) {   // r is warp-uniform: one branch per warp, no table loads; r = 0 multiplies nothing
+    case 0: load_pre_twiddled<Q, P, 0>(Ep, ja, x); break;
+    case 1: load_pre_twiddled<Q, P, 1>(Ep, ja, x); break;
+    case 2: load_pre_twiddled<Q, P, 2>(Ep, ja, x); break;
+    default: load_pre_twiddled<Q, P, 3>(Ep, ja, x); break;
+  }
+  if constexpr (P >= 32) {
+    w0 = __ldg(t1 + (r * Q) * P + ja);
+    v1 = __ldg(t1 + P + ja);
+  }
   dft<Q, +1>(x);
   const float2 v2 = cmul(v1, v1), v3 = cmul(v2, v1), v4 = cmul(v2, v2);
   float2 a = w0;
@@ -1025,7 +1085,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       const int ja = tid % P;
       float2 x[Q];
       const float2* Ep = E + pol * M;
-      pass1_task<N_>(Ep, ja, r, ev.t1, x);
+      pass1_task<N_>(Ep, ja, r, ev.k_lo, ev.t1, x);
       if (tid == 0) tma_bulk_wait_read();   // the previous pair's staged outputs have left A
       __syncthreads();   // every E read done: A may overwrite it
       const int row = (ev.k_lo + ja) % P;
@@ -1046,7 +1106,9 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     float bv = -1.0f;
     int bi = 0;
     if constexpr (SPLIT == 1) {
-      const int r = tid & 3, mb = tid >> 2;
+      const int r = tid & 3, mb = tid >> 2;   // 4 mb + r == tid
+      // the output twiddles of pass 1's rows, tau_i = c u^i (see pass1_task)
+      const float2 c = __ldg(ev.t1 + 4 * Q * P + tid), u1 = __ldg(ev.t1 + 4 * Q * P + T + tid);
       float2 y0[P], y1[P];
       const float2* src0 = A + r * PLN + mb;
       const float2* src1 = A + (4 + r) * PLN + mb;
@@ -1055,6 +1117,23 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
         y1[i] = src1[i * LDA];
       });
       __syncthreads();   // every A read done: the staging area may overwrite it
+      {
+        const float2 u2 = cmul(u1, u1), u3 = cmul(u2, u1), u4 = cmul(u2, u2);
+        float2 a = c;   // tau_{4I}
+        static_for<0, P / 4>([&](auto ii) {
+          constexpr int I = decltype(ii)::value;
+          const float2 w1 = cmul(a, u1), w2 = cmul(a, u2), w3 = cmul(a, u3);
+          y0[4 * I] = cmul(y0[4 * I], a);
+          y1[4 * I] = cmul(y1[4 * I], a);
+          y0[4 * I + 1] = cmul(y0[4 * I + 1], w1);
+          y1[4 * I + 1] = cmul(y1[4 * I + 1], w1);
+          y0[4 * I + 2] = cmul(y0[4 * I + 2], w2);
+          y1[4 * I + 2] = cmul(y1[4 * I + 2], w2);
+          y0[4 * I + 3] = cmul(y0[4 * I + 3], w3);
+          y1[4 * I + 3] = cmul(y1[4 * I + 3], w3);
+          if constexpr (I + 1 < P / 4) a = cmul(a, u4);
+        });
+      }
       dft<P, +1>(y0);
       dft<P, +1>(y1);
       static_for<0, P>([&](auto ma) {

@@ -103,13 +103,15 @@ def test_parity_direction_scan_full_size_sampled(ctx, pat, pid):
 def test_edge_directions(ctx, pat, pid):
     dirs = np.array([[math.radians(30), math.radians(45)], [float("nan"), 0.1], [0.2, float("inf")],
                      [math.radians(97.0), 1.0], [-0.05, 2.0], [math.radians(20), -7.5],
-                     [math.radians(59.9), 4 * math.pi + 0.3], [math.radians(90), math.radians(355)]])
+                     [math.radians(59.9), 4 * math.pi + 0.3], [math.radians(90), math.radians(355)],
+                     [0.3, 1e300], [0.4, -1.7e308]])   # azimuths too large to reduce: no cell
     ev = synth.make_event(4, 2048, dirs, seed_key=21)
     gpu = run_gpu(ctx, pid, ev)
     ref = oracle.unfold_event(pat, ev)
     check_event(gpu, ref, ev)
-    assert np.all(gpu["status"][1:3] == oracle.ST_BAD_DIR)
+    assert np.all(gpu["status"][1:3] == oracle.ST_BAD_DIR) and np.all(gpu["status"][8:10] == oracle.ST_BAD_DIR)
     assert np.all(gpu["efield"][1:3] == 0) and np.all(gpu["peak_idx"][1:3] == 0)
+    assert np.all(gpu["efield"][8:10] == 0) and np.all(gpu["envelope"][8:10] == 0)
     assert np.all(gpu["status"][3:5] & oracle.ST_ZEN_CLAMP)
 
 

@@ -182,7 +182,8 @@ def test_reconstruction_takes_the_ids(env):
     args = (_dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns))
     plain = ctx.reconstruct(ids[1], *args, ev.fs_hz, max_iter=6)
     sp = _dev(np.full(40, ids[1], np.int32))
-    e = binding.make_event(ids[0], *args, torch.empty((1, 2), dtype=torch.float64, device="cuda"), ev.fs_hz, 1.0, sp)
+    unused_dirs = torch.zeros((1, 2), dtype=torch.float64, device="cuda")   # the event holds raw pointers
+    e = binding.make_event(ids[0], *args, unused_dirs, ev.fs_hz, 1.0, sp)
     # the binding's reconstruct builds its own event; run the ABI call directly with the ids
     last, _ = binding.alloc_outputs(1, 40, 2048, device="cuda")
     res = dict(direction=torch.empty(2, dtype=torch.float64, device="cuda"),

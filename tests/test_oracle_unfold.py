@@ -184,6 +184,24 @@ def test_bad_direction():
     assert o["status"] & oracle.ST_BAD_DIR and np.all(o["efield"] == 0) and o["peak_idx"] == 0
 
 
+def test_unreducible_azimuth_is_a_bad_direction():
+    """An azimuth 2^52 or more azimuth steps from az0 (one FP64 unit is then a whole step)
+    has no cell: it is flagged like a non-finite one. 1000 turns plus 0.3 rad still reduce,
+    to the direction at 0.3 rad (the azimuth axis is periodic)."""
+    rng = np.random.default_rng(5)
+    n = 256
+    tr = rng.standard_normal((2, n)).astype(np.float32)
+    pat = synth.make_pattern()
+    daz = pat.daz_rad
+    for az in (1e300, -1.7e308, 2.0 ** 54 * daz, -(2.0 ** 54) * daz):
+        o = oracle.unfold_pair(pat, tr, 0.3, az, FS)
+        assert o["status"] & oracle.ST_BAD_DIR and np.all(o["efield"] == 0) and np.all(o["env"] == 0)
+    o = oracle.unfold_pair(pat, tr, 0.3, 2000 * math.pi + 0.3, FS)   # 72000 azimuth steps
+    assert not o["status"] & oracle.ST_BAD_DIR
+    ref = oracle.unfold_pair(pat, tr, 0.3, 0.3, FS)
+    assert np.allclose(o["efield"], ref["efield"], rtol=1e-9, atol=1e-9 * np.abs(ref["efield"]).max())
+
+
 # ---- residual ----------------------------------------------------------------------
 
 C = 0.299792458  # m/ns
