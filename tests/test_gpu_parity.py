@@ -100,6 +100,22 @@ def test_parity_direction_scan_full_size_sampled(ctx, pat, pid):
         assert abs(gpu["chi2"][d] - chi2) <= 1e-9 * max(chi2, 1.0)
 
 
+# Sampling rates whose band window starts at every kind of k_lo modulo the pass-2 size P (16
+# at 1024 and 2048 samples, 32 at 4096): the band rows past k_lo mod P are the ones the
+# inverse transform treats separately (at 2048 samples a one-slot input shift in pass 1).
+# k_lo mod P: 2048 -> 240 MHz 0, 213 MHz 1, 204.8 MHz 12, 227 MHz 15; 1024 -> 240 MHz 0,
+# 213 MHz 1, 227 MHz 8; 4096 -> 240 MHz 0, 233 MHz 16, 227 MHz 30.
+@pytest.mark.parametrize("n,fs_mhz", [(2048, 240.0), (2048, 213.0), (2048, 204.8), (2048, 227.0),
+                                      (1024, 240.0), (1024, 213.0), (1024, 227.0),
+                                      (4096, 240.0), (4096, 233.0), (4096, 227.0)])
+def test_parity_band_offsets(ctx, pat, pid, n, fs_mhz):
+    rng = np.random.default_rng(int(fs_mhz * 10) + n)
+    ev = synth.make_event(6, n, synth.random_directions(4, rng), seed_key=40 + n // 1024, fs_hz=fs_mhz * 1e6)
+    gpu = run_gpu(ctx, pid, ev)
+    ref = oracle.unfold_event(pat, ev)
+    check_event(gpu, ref, ev)
+
+
 def test_edge_directions(ctx, pat, pid):
     dirs = np.array([[math.radians(30), math.radians(45)], [float("nan"), 0.1], [0.2, float("inf")],
                      [math.radians(97.0), 1.0], [-0.05, 2.0], [math.radians(20), -7.5],

@@ -53,6 +53,16 @@ def test_x6_meets_the_parity_bar(env, n, s, d):
     check_event(gpu, ref, ev)
 
 
+@pytest.mark.parametrize("n,fs_mhz", [(2048, 227.0), (1024, 240.0), (4096, 233.0)])
+def test_x6_parity_off_the_default_band_offset(env, n, fs_mhz):
+    """Sampling rates whose band starts at k_lo = 271 (2048), 128 (1024) and 528 (4096)
+    instead of the 200 MHz windows: the transform tables follow k_lo."""
+    binding, ctx, pat, pid = env
+    rng = np.random.default_rng(n + int(fs_mhz))
+    ev = synth.make_event(5, n, synth.random_directions(3, rng), seed_key=960 + n // 1024, fs_hz=fs_mhz * 1e6)
+    check_event(_run(ctx, pid, ev, 6), oracle.unfold_event(pat, ev), ev)
+
+
 def test_x3_error_on_the_single_event(env):
     binding, ctx, pat, pid = env
     ev = synth.single_event(n_samples=4096)

@@ -2,8 +2,8 @@
 
 Such callers (a real-time acquisition loop whose device memory map is fixed after start-up,
 a plug-in inside another program's CUDA context) get the same unfolding from a fixed scratch
-array inside the library. This test calls it through the C ABI twice in a row, on two events
-of different shapes, and compares each result with ar_unfold's on the same inputs, within the
+array inside the library. This test calls it through the C ABI three times in a row, on
+events of different shapes and sampling rates, and compares each result with ar_unfold's on the same inputs, within the
 tolerances of the parity tests. It also checks that an event beyond the scratch limit is
 refused with a message. Collected last (file name) so that a failure here stops a -x run only
 after every other test has run; it needs nothing from the other tests.
@@ -55,20 +55,22 @@ def test_noalloc_matches_ar_unfold_on_two_calls_in_a_row():
     table = _dev(pat.table)            # the caller's own device copy of the VEL table
     rng = np.random.default_rng(99)
     events = [synth.make_event(9, 2048, synth.random_directions(5, rng), seed_key=91),
-              synth.make_event(4, 1024, synth.random_directions(3, rng), seed_key=92)]
+              synth.make_event(4, 1024, synth.random_directions(3, rng), seed_key=92),
+              # 227 MHz: the band starts at k_lo = 271, 15 mod 16 (the device-built twiddles)
+              synth.make_event(5, 2048, synth.random_directions(3, rng), seed_key=93, fs_hz=227e6)]
     stream = torch.cuda.current_stream()
     got_all = []
     for ev in events:                  # two calls in a row on the shared scratch array
         tr, pos, ts, dirs = _dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns), _dev(ev.dirs_rad)
         out, st = binding.alloc_outputs(ev.n_dirs, ev.n_stations, ev.n_samples)
-        binding.ar_unfold_noalloc(pat.desc(), table.data_ptr(), binding.make_event(-1, tr, pos, ts, dirs), st,
-                                  stream.cuda_stream)
+        binding.ar_unfold_noalloc(pat.desc(), table.data_ptr(), binding.make_event(-1, tr, pos, ts, dirs, ev.fs_hz),
+                                  st, stream.cuda_stream)
         got_all.append(out)
     torch.cuda.synchronize()
     for ev, out in zip(events, got_all):
         got = {k: v.cpu().numpy() for k, v in out.items()}
         ref = {k: v.cpu().numpy() for k, v in ctx.unfold(pid, _dev(ev.traces), _dev(ev.pos_m), _dev(ev.t_start_ns),
-                                                         _dev(ev.dirs_rad), sync=True).items()}
+                                                         _dev(ev.dirs_rad), fs_hz=ev.fs_hz, sync=True).items()}
         _compare(got, ref, ev.n_samples)
     ctx.close()
 
