@@ -32,6 +32,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -51,9 +52,14 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "unfold_kernel_traffic.json")
 
 
 def kernel_source_hash() -> str:
+    """Hash of the unfold kernel's source with comments and blank lines removed, so that the
+    recorded ncu traffic stays attached to the code it was measured on across comment edits."""
     h = hashlib.sha256()
     for f in ("kernels.cuh", "dft.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1507_07733_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1507_07733_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -501,11 +501,11 @@ __device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double ze
   return di;
 }
 
-// Pre-twiddles of pass 1, exp(2 pi i jb r / 4Q) at [r][jb], for Q = 32 and Q = 16. They are
-// read with a warp-uniform r so that one copy of the pass-1 code serves all four r: the
-// kernel is limited by instruction fetch when the four variants are compiled separately.
-// pass-1 load with pre-twiddle: x[jb] = E_p[ja + P jb] exp(2 pi i jb R / 4Q) for one residue R,
-// the twiddles compile-time constants
+// Pass-1 loads with pre-twiddle, x[jb] = E_p[ja + P jb] exp(2 pi i jb R / 4Q) for one residue
+// R, the twiddles compile-time constants (R = 0 multiplies nothing). The caller branches on
+// the warp-uniform r, so a branch holds only these loads and products and the DFT after it
+// stays one code path (four full copies of pass 1 made the kernel limited by instruction
+// fetch).
 template <int Q, int P, int R>
 __device__ __forceinline__ void load_pre_twiddled(const float2* Ep, int ja, float2 (&x)[Q]) {
   static_for<0, Q>([&](auto jb) {
