@@ -138,6 +138,18 @@ float2 unit(long t, long n, int sign) {   // exp(sign * 2 pi i t / n), t reduced
   return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(sign * std::sin(a)));
 }
 
+// the pass-1 pre-twiddles exp(2 pi i jb r / 4Q) of the 1024- and 4096-sample layouts into the
+// kernels' constant tables (current device)
+cudaError_t upload_pretwiddles() {
+  float2 a[4][32], b[4][16];
+  for (int r = 0; r < 4; ++r) {
+    for (int j = 0; j < 32; ++j) a[r][j] = unit(static_cast<long>(j) * r, 128, +1);
+    for (int j = 0; j < 16; ++j) b[r][j] = unit(static_cast<long>(j) * r, 64, +1);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_pre32, a, sizeof a);
+  return e != cudaSuccess ? e : cudaMemcpyToSymbol(c_pre16, b, sizeof b);
+}
+
 template <int N_>
 ar_status build_len_tables(ar_ctx* ctx, int k_lo, LenTables* lt) {
   using L = Layout<N_>;
@@ -566,7 +578,7 @@ ar_status ar_create(ar_ctx** out, const ar_config* cfg) {
   ctx->cfg = c;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess || upload_pretwiddles() != cudaSuccess) {
     delete ctx;
     return create_fail(AR_ERR_OUT_OF_MEMORY, "context allocation failed");
   }
@@ -1993,6 +2005,7 @@ ar_status noalloc_setup(int dev, NoAllocDevice** out) {
   if (!d.ready) {
     void* p = nullptr;
     AR_NA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    AR_NA_CUDA(upload_pretwiddles());
     AR_NA_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t sp1 = SpectrumSmem<1024>::TOTAL;
     const size_t sp2 = SpectrumSmem<2048>::TOTAL;

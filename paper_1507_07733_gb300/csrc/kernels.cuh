@@ -501,23 +501,21 @@ __device__ __forceinline__ DirInfo direction_cell(const PatternRef& p, double ze
   return di;
 }
 
-// Pass-1 loads with pre-twiddle, x[jb] = E_p[ja + P jb] exp(2 pi i jb R / 4Q) for one residue
-// R, the twiddles compile-time constants (R = 0 multiplies nothing). The caller branches on
-// the warp-uniform r, so a branch holds only these loads and products and the DFT after it
-// stays one code path (four full copies of pass 1 made the kernel limited by instruction
-// fetch).
-template <int Q, int P, int R>
-__device__ __forceinline__ void load_pre_twiddled(const float2* Ep, int ja, float2 (&x)[Q]) {
-  static_for<0, Q>([&](auto jb) {
-    constexpr long JB = decltype(jb)::value;
-    x[JB] = twmul<JB * R, 4 * Q, +1>(Ep[ja + P * JB]);
-  });
-}
+// Pre-twiddles of pass 1 for the 1024- and 4096-sample layouts, exp(2 pi i jb r / 4Q) at
+// [r][jb] (Q = 16 and 32), read with a warp-uniform r so that one copy of their pass-1 code
+// serves all four r. Per-r copies made the 2048-sample scan 1 % faster alone, but a batch graph
+// runs the three lengths' kernels side by side and larger code there cost more than it saved.
+__constant__ float2 c_pre32[4][32];
+__constant__ float2 c_pre16[4][16];
 
-// The same with the output twiddle's band wrap absorbed: for sh = 1 the task's rows carry an
-// extra factor exp(2 pi i (4 mb + r) / 4Q) = exp(2 pi i mb / Q) exp(2 pi i r / 4Q), a cyclic
-// shift of the DFT input by one slot: slot jb reads E_p[ja + P (jb - 1)] with the slot's own
-// pre-twiddle, and slot 0 reads E_p[ja + P (Q - 1)] turned by i^R.
+// Pass-1 loads of the 2048-sample layout with pre-twiddle, x[jb] = E_p[ja + P jb]
+// exp(2 pi i jb R / 4Q) for one residue R as compile-time constants (R = 0 multiplies
+// nothing), the caller branching on the warp-uniform r; the DFT after them stays one code path
+// (four full copies of pass 1 made the kernel limited by instruction fetch). The output
+// twiddle's band wrap is absorbed here: for sh = 1 the task's rows carry an extra factor
+// exp(2 pi i (4 mb + r) / 4Q) = exp(2 pi i mb / Q) exp(2 pi i r / 4Q), a cyclic shift of the DFT
+// input by one slot: slot jb reads E_p[ja + P (jb - 1)] with the slot's own pre-twiddle, and
+// slot 0 reads E_p[ja + P (Q - 1)] turned by i^R.
 template <int Q, int P, int R>
 __device__ __forceinline__ void load_pre_twiddled_wrap(const float2* Ep, int ja, bool sh, float2 (&x)[Q]) {
   const int b = sh ? ja - P : ja;   // slot jb >= 1 reads b + P jb (always in [0, P Q))
@@ -562,21 +560,18 @@ __device__ __forceinline__ void pass1_task(const float2* Ep, int ja, int r, int 
     dft<Q, +1>(x);
     return;
   }
-  float2 w0, v1;   // issued early (used after the DFT) where the registers allow
-  if constexpr (P < 32) {
-    w0 = __ldg(t1 + (r * Q) * P + ja);
-    v1 = __ldg(t1 + P + ja);
-  }
-  switch (r) {   // r is warp-uniform: one branch per warp, no table loads; r = 0 multiplies nothing
-    case 0: load_pre_twiddled<Q, P, 0>(Ep, ja, x); break;
-    case 1: load_pre_twiddled<Q, P, 1>(Ep, ja, x); break;
-    case 2: load_pre_twiddled<Q, P, 2>(Ep, ja, x); break;
-    default: load_pre_twiddled<Q, P, 3>(Ep, ja, x); break;
-  }
-  if constexpr (P >= 32) {
-    w0 = __ldg(t1 + (r * Q) * P + ja);
-    v1 = __ldg(t1 + P + ja);
-  }
+  static_assert(Q == 32 || Q == 16, "pre-twiddle tables exist for Q = 16 and 32");
+  const float2 w0 = __ldg(t1 + (r * Q) * P + ja);   // issued early: used after the DFT
+  const float2 v1 = __ldg(t1 + P + ja);
+  static_for<0, Q>([&](auto jb) {
+    constexpr int JB = decltype(jb)::value;
+    const float2 e = Ep[ja + P * JB];
+    if constexpr (JB == 0) {
+      x[JB] = e;
+    } else {
+      x[JB] = cmul(e, Q == 32 ? c_pre32[r][JB] : c_pre16[r][JB]);
+    }
+  });
   dft<Q, +1>(x);
   const float2 v2 = cmul(v1, v1), v3 = cmul(v2, v1), v4 = cmul(v2, v2);
   float2 a = w0;

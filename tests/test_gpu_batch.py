@@ -44,9 +44,13 @@ def _plain(binding, ctx, pid, ev, inputs):
 def test_batch_equals_plain_bit_for_bit(setup):
     binding, ctx, pat, pid = setup
     rng = np.random.default_rng(5)
-    descs = [(3, 1024, 16, 701), (17, 4096, 5, 702), (124, 2048, 3, 703), (9, 1024, 40, 704),
-             (1, 2048, 1, 705), (33, 4096, 2, 706), (64, 2048, 11, 707), (5, 1024, 1, 708)]
-    evs = [synth.make_event(S, N, synth.random_directions(D, rng), seed_key=k) for S, N, D, k in descs]
+    # (stations, samples, directions, seed, sampling rate in MHz): three events off the 200 MHz
+    # band window, so that one launch walks events with different k_lo and twiddle tables
+    descs = [(3, 1024, 16, 701, 200.0), (17, 4096, 5, 702, 200.0), (124, 2048, 3, 703, 227.0),
+             (9, 1024, 40, 704, 200.0), (1, 2048, 1, 705, 200.0), (33, 4096, 2, 706, 233.0),
+             (64, 2048, 11, 707, 240.0), (5, 1024, 1, 708, 200.0)]
+    evs = [synth.make_event(S, N, synth.random_directions(D, rng), seed_key=k, fs_hz=f * 1e6)
+           for S, N, D, k, f in descs]
     inputs = [_upload(e) for e in evs]
     plan = ctx.batch(16, 400, 200, 51)
     outs = [binding.alloc_outputs(e.n_dirs, e.n_stations, e.n_samples)[0] for e in evs]
