@@ -22,7 +22,8 @@
 // Pass 1 is a Q-point DFT per (polarisation, r, ja); pass 2 a P-point DFT per (r, mb). The
 // output phase of the band offset is absorbed by rotating pass 2's input rows by k_lo mod P,
 // so no per-sample phase is applied at the end, and thread t of pass 2 writes samples
-// n = t + 4Q ma: every warp store is 128 contiguous bytes.
+// n = t + 4Q ma: every warp store is 128 contiguous bytes. At N = 2048, where one pass-2
+// thread holds both polarisations, T1 is applied in pass 2 instead (see pass1_task).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
