@@ -146,8 +146,8 @@ ar_status ar_create(ar_ctx** ctx, const ar_config* cfg);
 ar_status ar_destroy(ar_ctx* ctx);
 
 /* Message of the last failing call on ctx ("" if none). Valid until the next call on ctx.
- * ctx NULL gives the message of the last failing ar_create or ar_unfold_noalloc in this
- * process. */
+ * ctx NULL gives the message of the last failing ar_create or ar_unfold_noalloc made by the
+ * calling thread (each thread keeps its own; valid until that thread's next failing call). */
 const char* ar_last_error(const ar_ctx* ctx);
 
 /* Name of a status code. */
@@ -213,6 +213,17 @@ ar_status ar_sync(ar_ctx* ctx, void* stream);
  * when the outputs are in the caller's host arrays. Host arrays may be pageable; pinned
  * memory makes the copies faster. Errors: as ar_unfold, plus AR_ERR_DEVICE. */
 ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream);
+
+/* Test of the error path of the kernels' bounded waits (not in the paper; for tests only).
+ * mode 1: until set back to 0, ar_unfold's unfold kernel gives its corner-slab waits a limit
+ * of 1 ms and has each slab mbarrier expect 16 bytes more than its four bulk copies deliver
+ * (the copies themselves are unchanged and in bounds), so wherever the kernel stages the
+ * slabs in shared memory (patterns whose slabs fit beside the CTAs per SM; larger ones are
+ * read from L2 without a wait) each wait runs out: the kernel sets the error
+ * word and its CTAs return early, the outputs of that call are undefined, and ar_sync reports
+ * AR_ERR_DEVICE (bit 0). The context stays usable; the next call with mode 0 is normal.
+ * Errors: AR_ERR_INVALID_ARG (NULL ctx, mode not 0 or 1). */
+ar_status ar_set_test_fault(ar_ctx* ctx, int32_t mode);
 
 /* Per-kernel timing. While enabled, ar_unfold records CUDA events on its stream around each
  * of its kernels (which keeps the second kernel from starting before the first ends).

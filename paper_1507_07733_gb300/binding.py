@@ -33,6 +33,7 @@ AR_STATUS_BAD_PATTERN = 8
 #: every symbol include/aerafold.h declares
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
+            "ar_set_test_fault",
             "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy",
             "ar_server_create", "ar_submit", "ar_poll", "ar_wait", "ar_ticket_times", "ar_ticket_release",
             "ar_server_destroy", "ar_reconstruct", "ar_unfold_tc"]
@@ -101,7 +102,8 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        # AERAFOLD_LIB selects another build of the library (the debug build in the tests)
+        p = path or os.environ.get("AERAFOLD_LIB") or LIB_PATH
         if not os.path.exists(p):
             raise LibraryMissing(f"{p} not found: build it with __graft_entry__.build()")
         L = ctypes.CDLL(p)
@@ -119,6 +121,7 @@ def load(path: str | None = None):
         L.ar_sync.argtypes = [vp, vp]
         L.ar_unfold_host.argtypes = [vp, ctypes.POINTER(ar_event), ctypes.POINTER(ar_outputs), vp]
         L.ar_set_profiling.argtypes = [vp, i32]
+        L.ar_set_test_fault.argtypes = [vp, i32]
         L.ar_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.ar_batch_create.argtypes = [vp, ctypes.POINTER(ar_batch_limits), ctypes.POINTER(vp)]
         L.ar_batch_run.argtypes = [vp, vp, vp, i32, vp]
@@ -190,6 +193,11 @@ def ar_unfold(ctx, ev: ar_event, out: ar_outputs, stream: int = 0) -> None:
 def ar_unfold_tc(ctx, ev: ar_event, out: ar_outputs, split_terms: int = 3, stream: int = 0) -> None:
     _check(ctx, load().ar_unfold_tc(ctx, ctypes.byref(ev), ctypes.byref(out), int(split_terms),
                                     ctypes.c_void_p(stream)))
+
+
+def ar_set_test_fault(ctx, mode: int) -> None:
+    """Test of the bounded-wait error path (see include/aerafold.h)."""
+    _check(ctx, load().ar_set_test_fault(ctx, int(mode)))
 
 
 def ar_sync(ctx, stream: int = 0) -> None:

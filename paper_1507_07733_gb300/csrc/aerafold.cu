@@ -5,6 +5,7 @@
 // pattern) frequency-cell tables, a workspace arena for the station spectra (the paper's
 // shared static device buffers of Sec. 4, kept resident here), and a device error word.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -29,6 +30,15 @@ using namespace aerafold;
 
 namespace {
 
+// An NVTX range for profilers (Nsight Systems, ncu --nvtx) around each entry point's host
+// work and launches and around the server's steps; no cost without a profiler attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 constexpr double kBandLoHz = 30e6;
 constexpr double kBandHiHz = 80e6;
 constexpr double kCMPerNs = 0.299792458;
@@ -50,8 +60,9 @@ struct KernelCfg {
   int slab_direct = 0;   // corner slabs read from L2 (when staging them would cost occupancy)
 };
 
-std::mutex g_create_mu;
-std::string g_create_error;
+// the message ar_last_error(NULL) returns: the last failing ar_create or ar_unfold_noalloc of
+// the calling thread (one per thread, so a failure on another thread never rewrites it)
+thread_local std::string g_create_error;
 
 }  // namespace
 
@@ -82,6 +93,7 @@ struct ar_ctx {
   std::vector<std::pair<void*, size_t>> stage;   // slots, grown on demand
   // per-kernel timing
   bool profiling = false;
+  int test_fault = 0;        // ar_set_test_fault: 1 makes ar_unfold's corner-slab waits run out
   bool timed = false;
   bool timed_tc = false;   // the last timed call was ar_unfold_tc (four events)
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -474,12 +486,13 @@ EventDesc make_desc(const PathBuffers& b, const ar_pattern_desc& pd, const float
 // their first corner slabs before they wait for the spectra.
 template <int N_>
 cudaError_t launch_path(unsigned* err, const EventDesc& desc, int grid_cap, cudaStream_t stream,
-                        cudaEvent_t* evs /* 3 events or null */) {
+                        cudaEvent_t* evs /* 3 events or null */, int test_wait = 0) {
   using L = Layout<N_>;
   PathParams pp{};
   pp.batch = nullptr;
   pp.err = err;
   pp.wait_prior = 1;
+  pp.test_wait = test_wait;
   pp.ev0 = desc;
   cudaError_t e;
   if (evs && (e = cudaEventRecord(evs[0], stream)) != cudaSuccess) return e;
@@ -506,7 +519,8 @@ ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, con
   ar_status st = attach_patterns(ctx, ev, rs.k_lo, &desc);
   if (st != AR_OK) return st;
   desc.slab_direct = rs.kc->slab_direct;
-  cudaError_t e = launch_path<N_>(ctx->d_err, desc, rs.kc->grid, stream, ctx->profiling ? ctx->ev : nullptr);
+  cudaError_t e = launch_path<N_>(ctx->d_err, desc, rs.kc->grid, stream, ctx->profiling ? ctx->ev : nullptr,
+                                  ctx->test_fault);
   if (e != cudaSuccess) return fail(ctx, AR_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
   if (ctx->profiling) {
     ctx->timed = true;
@@ -515,25 +529,56 @@ ar_status launch_all(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, con
   return AR_OK;
 }
 
-ar_status check_event(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out) {
-  if (!ev || !out) return fail(ctx, AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+// The checks of a pattern descriptor that ar_load_pattern and ar_unfold_noalloc share: false
+// if it is valid, else true with the reason in why.
+bool pattern_desc_error(const ar_pattern_desc* d, char* why, size_t n) {
+  if (d->n_zen < 2 || d->n_az < 2 || d->n_freq < 2 || d->n_freq > kMaxFreqNodes) {
+    snprintf(why, n, "pattern sizes %d x %d x %d out of range", d->n_zen, d->n_az, d->n_freq);
+    return true;
+  }
+  if (!(d->dzen_rad > 0) || !(d->daz_rad > 0) || !(d->df_hz > 0) || !std::isfinite(d->dzen_rad) ||
+      !std::isfinite(d->daz_rad) || !std::isfinite(d->df_hz) || !std::isfinite(d->zen0_rad) ||
+      !std::isfinite(d->az0_rad) || !std::isfinite(d->f0_hz)) {
+    snprintf(why, n, "pattern axis steps must be positive and finite, origins finite");
+    return true;
+  }
+  if (std::fabs(d->n_az * d->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI) {
+    snprintf(why, n, "azimuth axis must cover 2 pi (n_az * daz = %.17g)", d->n_az * d->daz_rad);
+    return true;
+  }
+  const size_t nodes = static_cast<size_t>(d->n_zen) * d->n_az * d->n_freq;
+  if (nodes * 4 > (1ull << 31)) {
+    snprintf(why, n, "pattern too large (%zu nodes)", nodes);
+    return true;
+  }
+  return false;
+}
+
+// The checks of an event and its outputs that every entry point shares (the trace length and
+// rate are checked with the band window): false if they pass, else true with the reason.
+bool event_error(const ar_event* ev, const ar_outputs* out, char* why, size_t n) {
+  if (!ev || !out) return snprintf(why, n, "event and outputs must not be NULL"), true;
   if (ev->n_stations < 1 || ev->n_stations > (1 << 20))
-    return fail(ctx, AR_ERR_INVALID_ARG, "n_stations=%d out of [1, 2^20]", ev->n_stations);
-  if (ev->n_dirs < 1 || ev->n_dirs > (1 << 20))
-    return fail(ctx, AR_ERR_INVALID_ARG, "n_dirs=%d out of [1, 2^20]", ev->n_dirs);
+    return snprintf(why, n, "n_stations=%d out of [1, 2^20]", ev->n_stations), true;
+  if (ev->n_dirs < 1 || ev->n_dirs > (1 << 20)) return snprintf(why, n, "n_dirs=%d out of [1, 2^20]", ev->n_dirs), true;
   if (!ev->traces || !ev->pos_m || !ev->t_start_ns || !ev->dirs_rad)
-    return fail(ctx, AR_ERR_INVALID_ARG, "event arrays must not be NULL");
-  if (reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0)
-    return fail(ctx, AR_ERR_INVALID_ARG, "traces must be 16-byte aligned");
+    return snprintf(why, n, "event arrays must not be NULL"), true;
+  if (reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0) return snprintf(why, n, "traces must be 16-byte aligned"), true;
   if (!out->peak_idx || !out->peak_amp || !out->peak_time_ns || !out->residual_ns || !out->t0_ns || !out->chi2 ||
       !out->status)
-    return fail(ctx, AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
+    return snprintf(why, n, "peak, residual and status outputs must not be NULL"), true;
   if (!(ev->refractive_index >= 0.0) || !std::isfinite(ev->refractive_index))
-    return fail(ctx, AR_ERR_INVALID_ARG, "refractive_index must be finite and >= 0");
+    return snprintf(why, n, "refractive_index must be finite and >= 0"), true;
   if (reinterpret_cast<uintptr_t>(out->efield) % 16 != 0 || reinterpret_cast<uintptr_t>(out->envelope) % 16 != 0)
-    return fail(ctx, AR_ERR_INVALID_ARG, "efield and envelope must be 16-byte aligned");
+    return snprintf(why, n, "efield and envelope must be 16-byte aligned"), true;
   if (!out->efield && out->envelope)
-    return fail(ctx, AR_ERR_INVALID_ARG, "envelope without efield is not supported (give both or neither)");
+    return snprintf(why, n, "envelope without efield is not supported (give both or neither)"), true;
+  return false;
+}
+
+ar_status check_event(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out) {
+  char why[256];
+  if (event_error(ev, out, why, sizeof why)) return fail(ctx, AR_ERR_INVALID_ARG, "%s", why);
   return AR_OK;
 }
 
@@ -566,7 +611,6 @@ ar_status ar_create(ar_ctx** out, const ar_config* cfg) {
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   auto create_fail = [&](ar_status st, const char* msg) {
-    std::lock_guard<std::mutex> lk(g_create_mu);
     g_create_error = msg;
     return st;
   };
@@ -614,25 +658,16 @@ ar_status ar_destroy(ar_ctx* ctx) {
 }
 
 const char* ar_last_error(const ar_ctx* ctx) {
-  if (!ctx) {
-    std::lock_guard<std::mutex> lk(g_create_mu);
-    return g_create_error.c_str();
-  }
+  if (!ctx) return g_create_error.c_str();
   return ctx->last_error.c_str();
 }
 
 ar_status ar_load_pattern(ar_ctx* ctx, const ar_pattern_desc* d, const float* host_table, int32_t* pattern_id) {
   if (!ctx) return AR_ERR_INVALID_ARG;
   if (!d || !host_table || !pattern_id) return fail(ctx, AR_ERR_INVALID_ARG, "NULL argument");
-  if (d->n_zen < 2 || d->n_az < 2 || d->n_freq < 2 || d->n_freq > kMaxFreqNodes)
-    return fail(ctx, AR_ERR_INVALID_ARG, "pattern sizes %d x %d x %d out of range", d->n_zen, d->n_az, d->n_freq);
-  if (!(d->dzen_rad > 0) || !(d->daz_rad > 0) || !(d->df_hz > 0) || !std::isfinite(d->zen0_rad) ||
-      !std::isfinite(d->az0_rad) || !std::isfinite(d->f0_hz))
-    return fail(ctx, AR_ERR_INVALID_ARG, "pattern axis steps must be positive and origins finite");
-  if (std::fabs(d->n_az * d->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
-    return fail(ctx, AR_ERR_INVALID_ARG, "azimuth axis must cover 2 pi (n_az * daz = %.17g)", d->n_az * d->daz_rad);
+  char why[256];
+  if (pattern_desc_error(d, why, sizeof why)) return fail(ctx, AR_ERR_INVALID_ARG, "%s", why);
   const size_t nodes = static_cast<size_t>(d->n_zen) * d->n_az * d->n_freq;
-  if (nodes * 4 > (1ull << 31)) return fail(ctx, AR_ERR_INVALID_ARG, "pattern too large");
   AR_CUDA(ctx, cudaSetDevice(ctx->device));
   PatternDev p;
   p.desc = *d;
@@ -658,6 +693,7 @@ ar_status ar_prepare(ar_ctx* ctx, int32_t n_samples, double fs_hz, int32_t patte
 }
 
 ar_status ar_unfold(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream) {
+  NvtxRange nvtx("ar_unfold");
   if (!ctx) return AR_ERR_INVALID_ARG;
   ar_status st = check_event(ctx, ev, out);
   if (st != AR_OK) return st;
@@ -733,6 +769,7 @@ extern "C" {
 
 ar_status ar_reconstruct(ar_ctx* ctx, const ar_event* ev, int32_t max_iter, double tol_rad, const ar_recon_out* out,
                          void* stream) {
+  NvtxRange nvtx("ar_reconstruct");
   if (!ctx) return AR_ERR_INVALID_ARG;
   if (!ev || !out) return fail(ctx, AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
   if (max_iter < 0 || max_iter > 64) return fail(ctx, AR_ERR_INVALID_ARG, "max_iter must be in [0, 64]");
@@ -788,13 +825,14 @@ ar_status ar_sync(ar_ctx* ctx, void* stream) {
     AR_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
     return fail(ctx, AR_ERR_DEVICE,
                 "device error 0x%x (bit 0: a bounded wait for a bulk copy ran out; bit 1: a kernel got a launch "
-                "configuration it does not take)",
+                "configuration it does not take; bit 2: an index check of the debug build failed)",
                 err);
   }
   return AR_OK;
 }
 
 ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, void* stream) {
+  NvtxRange nvtx("ar_unfold_host");
   if (!ctx) return AR_ERR_INVALID_ARG;
   ar_status st = check_event(ctx, ev, out);
   if (st != AR_OK) return st;
@@ -856,6 +894,13 @@ ar_status ar_unfold_host(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out,
   for (int i = 4; i < 16; ++i)
     if (hosts[i] && sizes[i]) AR_CUDA(ctx, cudaMemcpyAsync(hosts[i], dev(i), sizes[i], cudaMemcpyDeviceToHost, s));
   return ar_sync(ctx, stream);
+}
+
+ar_status ar_set_test_fault(ar_ctx* ctx, int32_t mode) {
+  if (!ctx) return AR_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return fail(ctx, AR_ERR_INVALID_ARG, "test fault mode %d: 0 or 1", mode);
+  ctx->test_fault = mode;
+  return AR_OK;
 }
 
 ar_status ar_set_profiling(ar_ctx* ctx, int32_t enable) {
@@ -1085,6 +1130,7 @@ cudaError_t launch_tc(ar_ctx* ctx, const EventDesc& ev, int terms, size_t rows_f
 extern "C" {
 
 ar_status ar_unfold_tc(ar_ctx* ctx, const ar_event* ev, const ar_outputs* out, int32_t split_terms, void* stream) {
+  NvtxRange nvtx("ar_unfold_tc");
   if (!ctx) return AR_ERR_INVALID_ARG;
   if (split_terms != 3 && split_terms != 6)
     return fail(ctx, AR_ERR_INVALID_ARG, "split_terms=%d: 3 or 6", split_terms);
@@ -1438,6 +1484,7 @@ static ar_status batch_autotune(ar_batch* b, int set, bool snr, cudaStream_t str
 
 ar_status ar_batch_run(ar_batch* b, const ar_event* events, const ar_outputs* outs, int32_t n_events,
                        void* stream) {
+  NvtxRange nvtx("ar_batch_run");
   if (!b) return AR_ERR_INVALID_ARG;
   ar_ctx* ctx = b->ctx;
   if (!events || !outs || n_events < 1) return fail(ctx, AR_ERR_INVALID_ARG, "events and outputs must not be empty");
@@ -1693,6 +1740,7 @@ void server_loop(ar_server* sv) {
       if (!L.busy) { slot = &L; break; }
     std::vector<uint64_t> batch;
     if (slot) {
+      NvtxRange nvtx("server admit");
       // admit in arrival order while the state fits the budget
       size_t stations = 0, dirs = 0;
       while (!sv->queue.empty() && static_cast<int>(batch.size()) < sv->cfg.max_batch_events) {
@@ -1725,6 +1773,7 @@ void server_loop(ar_server* sv) {
       continue;
     }
     // launch: inputs in, one batch run, outputs out
+    NvtxRange nvtx("server launch (copies in, batch run, copies out)");
     std::vector<ar_event> evs;
     std::vector<ar_outputs> outs;
     cudaError_t e = cudaSuccess;
@@ -1936,14 +1985,13 @@ struct NoAllocDevice {
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 std::mutex g_noalloc_mu;
 
-// failures are reported through the process-wide message that ar_last_error(NULL) returns
+// failures are reported through the calling thread's message that ar_last_error(NULL) returns
 ar_status noalloc_fail(ar_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
-  std::lock_guard<std::mutex> lk(g_create_mu);
   g_create_error = buf;
   return st;
 }
@@ -2066,14 +2114,14 @@ extern "C" {
 
 ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const ar_event* ev,
                             const ar_outputs* out, void* stream) {
+  NvtxRange nvtx("ar_unfold_noalloc");
   if (!pd || !table) return noalloc_fail(AR_ERR_INVALID_ARG, "pattern descriptor and table must not be NULL");
   if (reinterpret_cast<uintptr_t>(table) % 16 != 0)
     return noalloc_fail(AR_ERR_INVALID_ARG, "the VEL table must be 16-byte aligned");
-  if (pd->n_zen < 2 || pd->n_az < 2 || pd->n_freq < 2 || pd->n_freq > kMaxFreqNodes || !(pd->dzen_rad > 0) ||
-      !(pd->daz_rad > 0) || !(pd->df_hz > 0) ||
-      std::fabs(pd->n_az * pd->daz_rad - 2.0 * M_PI) > 1e-9 * 2.0 * M_PI)
-    return noalloc_fail(AR_ERR_INVALID_ARG, "bad pattern descriptor");
-  if (!ev || !out) return noalloc_fail(AR_ERR_INVALID_ARG, "event and outputs must not be NULL");
+  char why[256];
+  if (pattern_desc_error(pd, why, sizeof why)) return noalloc_fail(AR_ERR_INVALID_ARG, "%s", why);
+  // the checks ar_unfold makes, then the ones of the fixed scratch
+  if (event_error(ev, out, why, sizeof why)) return noalloc_fail(AR_ERR_INVALID_ARG, "%s", why);
   if (ev->station_pattern)
     return noalloc_fail(AR_ERR_INVALID_ARG, "per-station patterns need a context (ar_unfold); station_pattern must be NULL");
   if (ev->n_stations < 1 || ev->n_dirs < 1 || ev->n_dirs > kNoAllocMaxDirs)
@@ -2086,16 +2134,7 @@ ar_status ar_unfold_noalloc(const ar_pattern_desc* pd, const float* table, const
                         "n_stations x n_samples = %lld exceeds the fixed scratch of ar_unfold_noalloc "
                         "(at most %lld: 240 stations of 4096, 480 of 2048 or 960 of 1024 samples)",
                         static_cast<long long>(ev->n_stations) * ev->n_samples, kNoAllocMaxStationSamples);
-  if (!ev->traces || !ev->pos_m || !ev->t_start_ns || !ev->dirs_rad ||
-      reinterpret_cast<uintptr_t>(ev->traces) % 16 != 0)
-    return noalloc_fail(AR_ERR_INVALID_ARG, "event arrays must be non-NULL, traces 16-byte aligned");
-  if (!out->peak_idx || !out->peak_amp || !out->peak_time_ns || !out->residual_ns || !out->t0_ns || !out->chi2 ||
-      !out->status)
-    return noalloc_fail(AR_ERR_INVALID_ARG, "peak, residual and status outputs must not be NULL");
-  if (reinterpret_cast<uintptr_t>(out->efield) % 16 != 0 || reinterpret_cast<uintptr_t>(out->envelope) % 16 != 0 ||
-      (!out->efield && out->envelope))
-    return noalloc_fail(AR_ERR_INVALID_ARG, "efield and envelope must be 16-byte aligned, and given together");
-  if (!(ev->fs_hz > 0.0)) return noalloc_fail(AR_ERR_INVALID_ARG, "fs_hz must be positive");
+  if (!(ev->fs_hz > 0.0) || !std::isfinite(ev->fs_hz)) return noalloc_fail(AR_ERR_INVALID_ARG, "fs_hz must be positive");
   int lo, cnt, hi;
   band_window(ev->n_samples, ev->fs_hz, &lo, &cnt, &hi);
   if (cnt < 1 || cnt > ev->n_samples / 4 || lo + ev->n_samples / 4 > ev->n_samples / 2 || 2 * hi >= ev->n_samples)

@@ -38,7 +38,21 @@ constexpr unsigned kStBadDir = 4u;
 constexpr unsigned kStBadPattern = 8u;
 
 constexpr unsigned kErrTmaTimeout = 1u;     // a bounded mbarrier wait ran out
+constexpr unsigned kErrBounds = 4u;         // (debug build) an index check failed; the access was skipped
+
+// Index checks of the debug build (compiled with AR_DEBUG_BOUNDS): a failed check sets
+// kErrBounds in the error word, which ar_sync reports as AR_ERR_DEVICE, and the caller skips
+// the access instead of trapping. In the release build every check is the constant true.
+#ifdef AR_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(bool ok, unsigned* err) {
+  if (!ok && err) atomicOr(err, kErrBounds);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(bool, unsigned*) { return true; }
+#endif
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+constexpr unsigned long long kTestWaitLimitNs = 1000000ull;   // 1 ms: the limit under PathParams::test_wait
 
 // ---- shapes per trace length ------------------------------------------------------------
 
@@ -227,7 +241,11 @@ struct PathParams {
   unsigned* err;              // device error word
   const int* skip;            // if not null and *skip != 0 the kernel does nothing (a loop has converged)
   int wait_prior;             // wait for the previous kernel in the stream (its results are needed)
-  int pad;
+  // Test of the bounded-wait error path (ar_set_test_fault): nonzero makes every corner-slab
+  // mbarrier expect 16 bytes more than its four bulk copies deliver, and its waits give up
+  // after 1 ms, so the waits run out, the error word gets kErrTmaTimeout and the CTAs return.
+  // The copies themselves are unchanged and in bounds. 0 in every other launch.
+  int test_wait;
   EventDesc ev0;
 };
 
@@ -357,6 +375,7 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::BLOCK) station_spectrum_kern
     ev = evs + find_event(prm.batch->n_events, gs, [&](int e) { return static_cast<long long>(evs[e].station_begin); });
   }
   const int s = gs - ev->station_begin;
+  if (!in_bounds(s >= 0 && s < ev->n_st, prm.err)) continue;   // (uniform over the CTA)
   if (tid >= T) {
     if (ev->dir_pre) {
       // the previous kernel in the stream may still read the entries: wait before writing.
@@ -413,7 +432,7 @@ __global__ void __launch_bounds__(SpectrumSmem<N_>::BLOCK) station_spectrum_kern
       int rank = 0;
 #pragma unroll
       for (int w = 0; w < T / 32; ++w) rank += part[w];
-      ev->st_walk[rank] = make_int2(s, ks == np ? -2 : ks);
+      if (in_bounds(rank >= 0 && rank < S, prm.err)) ev->st_walk[rank] = make_int2(s, ks == np ? -2 : ks);
     }
   }
   // combine the four decimated transforms at k and N - k, split the channels
@@ -810,14 +829,20 @@ __device__ __forceinline__ bool slab_staged(const EventDesc& ev, int p) { return
 // With pre (after the wait for the station kernel) the event's own pattern's cell is taken
 // from the direction's precomputed entry instead of being formed here in FP64.
 __device__ __forceinline__ void issue_key(const EventDesc& ev, int d, int p, DirInfo* sdir, float2* slab,
-                                          uint64_t* bar, bool pre = false) {
+                                          uint64_t* bar, bool pre = false, unsigned* err = nullptr,
+                                          unsigned extra_tx = 0) {
   const PatternRef pr = pattern_ref(ev, p);
-  const DirInfo di = (pre && p == -1 && ev.dir_pre) ? load_cell(ev.dir_pre + d) : pair_cell(ev, d, p, nullptr);
+  DirInfo di = (pre && p == -1 && ev.dir_pre) ? load_cell(ev.dir_pre + d) : pair_cell(ev, d, p, nullptr);
+  const int cells = pr.n_zen * pr.n_az;
+  if (!in_bounds(di.slab0 >= 0 && di.slab0 < cells && di.slab1 >= 0 && di.slab1 < cells && di.slab2 >= 0 &&
+                     di.slab2 < cells && di.slab3 >= 0 && di.slab3 < cells,
+                 err))
+    di.st |= kStBadDir;   // (debug build) no corner is read; the key's outputs are zero
   *sdir = di;
   if (!slab_staged(ev, p)) return;
   const unsigned slab_bytes = static_cast<unsigned>(pr.n_f) * 4u * sizeof(float2);
   const size_t node = static_cast<size_t>(pr.n_f) * 4;
-  mbar_arrive_expect_tx(bar, 4 * slab_bytes);
+  mbar_arrive_expect_tx(bar, 4 * slab_bytes + extra_tx);
   tma_bulk_g2s(slab + 0 * node, pr.table + di.slab0 * node, slab_bytes, bar);
   tma_bulk_g2s(slab + 1 * node, pr.table + di.slab1 * node, slab_bytes, bar);
   tma_bulk_g2s(slab + 2 * node, pr.table + di.slab2 * node, slab_bytes, bar);
@@ -833,7 +858,7 @@ __device__ __forceinline__ void issue_key(const EventDesc& ev, int d, int p, Dir
 // T: the CTA's threads; direct: the corners are read from the table (else from slab).
 template <int N_, int T = Layout<N_>::T>
 __device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const DirInfo& di, const float2* slab,
-                                              bool direct, float2* hn, float4* hinv) {
+                                              bool direct, float2* hn, float4* hinv, unsigned* err = nullptr) {
   using L = Layout<N_>;
   constexpr int M = L::M, NB = M / T;
   static_assert(M % T == 0, "bins per thread");
@@ -880,21 +905,34 @@ __device__ __forceinline__ bool build_inverse(const EventDesc& ev, int p, const 
   for (int i = 0; i < NB; ++i) {
     const int j = tid + T * i;
     float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
-    const int2 bf = valid ? __ldg(pr.binf + j) : make_int2(-1, 0);
+    int2 bf = valid ? __ldg(pr.binf + j) : make_int2(-1, 0);
+    if (!in_bounds(bf.x < pr.n_f - 1, err)) bf.x = -1;   // a cell past the last node pair
     if (bf.x >= 0) {
       const float tf = __int_as_float(bf.y);
       const float4* g = reinterpret_cast<const float4*>(hn + 8 * bf.x);
       const float4 h01 = g[0], h23 = g[1], g01 = g[2], g23 = g[3];   // value, slope
-      const float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));    // H0t
-      const float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));    // H0p
-      const float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));    // H1t
-      const float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));   // H1p
+      float2 a = make_float2(fmaf(tf, g01.x, h01.x), fmaf(tf, g01.y, h01.y));    // H0t
+      float2 b = make_float2(fmaf(tf, g01.z, h01.z), fmaf(tf, g01.w, h01.w));    // H0p
+      float2 c = make_float2(fmaf(tf, g23.x, h23.x), fmaf(tf, g23.y, h23.y));    // H1t
+      float2 dd = make_float2(fmaf(tf, g23.z, h23.z), fmaf(tf, g23.w, h23.w));   // H1p
+      // Scale H by the power of two 2^(127 - e) that brings its largest component to [1, 2):
+      // exact, so the test and the inverse below give the same bits as unscaled wherever the
+      // unscaled forms neither overflow nor underflow, and they never do for |H| far from 1
+      // (the test compares fourth powers of |H|). The inverse is scaled back at the end.
+      const float hm = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))),
+                             fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fmaxf(fabsf(dd.x), fabsf(dd.y))));
+      const int ex = min(max(static_cast<int>((__float_as_uint(hm) >> 23) & 0xffu), 1), 253);
+      const float up = __uint_as_float(static_cast<unsigned>(254 - ex) << 23);    // 2^(127 - ex)
+      a = make_float2(a.x * up, a.y * up);
+      b = make_float2(b.x * up, b.y * up);
+      c = make_float2(c.x * up, c.y * up);
+      dd = make_float2(dd.x * up, dd.y * up);
       const float2 det = csub(cmul(a, dd), cmul(b, c));
       const float sc = sqrt_approx(cabs2(a) * cabs2(dd)) + sqrt_approx(cabs2(b) * cabs2(c));
       const float dd2 = cabs2(det);
       if (dd2 > 1e-12f * sc * sc) {
-        // X / det = X conj(det) / |det|^2
-        const float inv = kScale * rcp_approx(dd2);
+        // X / det = X conj(det) / |det|^2, times `up` for the scaling of H
+        const float inv = kScale * rcp_approx(dd2) * up;
         const float2 x00 = cmulc(dd, det), x01 = cmulc(b, det), x10 = cmulc(c, det), x11 = cmulc(a, det);
         h0 = make_float4(x00.x * inv, x00.y * inv, -x01.x * inv, -x01.y * inv);
         h1 = make_float4(-x10.x * inv, -x10.y * inv, x11.x * inv, x11.y * inv);
@@ -977,7 +1015,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
   }
   if (tid == 0) {
     mbar_init(bar, 1);
-    issue_key(evs[e0], d, p, sdir, slab, bar);
+    issue_key(evs[e0], d, p, sdir, slab, bar, false, prm.err, prm.test_wait ? 16u : 0u);
   }
   bool pending = slab_staged(evs[e0], p);   // slab copies to wait for before the next build
   __syncthreads();    // barrier initialised, first direction cell visible
@@ -991,17 +1029,23 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
   unsigned phase = 0;
   float4 vin[NB];            // the pair's station spectrum at this thread's bins (from L2)
   const auto load_spec = [&](const EventDesc& x, int st) {
+    if (!in_bounds(st >= 0 && st < x.n_st, prm.err)) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) vin[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      return;
+    }
     const float4* src = x.spec + static_cast<size_t>(st) * M + tid;
 #pragma unroll
     for (int i = 0; i < NB; ++i) vin[i] = __ldcg(src + T * i);
   };
   for (long long q = q0; q < q1; ++q) {
     if (pending) {
-      const bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
+      const unsigned long long limit = prm.test_wait ? kTestWaitLimitNs : kWaitLimitNs;
+      const bool ok = mbar_wait_bounded(bar, phase, limit);
       if (__syncthreads_or(!ok)) {   // a bulk copy never completed: report, give it one more bounded wait, leave
         if (tid == 0) {
           atomicOr(prm.err, kErrTmaTimeout);
-          mbar_wait_bounded(bar, phase, kWaitLimitNs);
+          mbar_wait_bounded(bar, phase, limit);
           tma_bulk_wait_all();
         }
         __syncthreads();
@@ -1036,7 +1080,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       di = *sdir;
       if (tid == 0) tma_bulk_wait_read();
       __syncthreads();
-      key_sing = build_inverse<N_>(ev, p, di, slab, ev.slab_direct != 0, hn, hinv);
+      key_sing = build_inverse<N_>(ev, p, di, slab, ev.slab_direct != 0, hn, hinv, prm.err);
       cur_e = e;
       cur_d = d;
       cur_p = p;
@@ -1070,7 +1114,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     const bool next_key = has_next && (dir_end || p_next != p);
     if (tid == 0 && next_key) {   // the next key's direction cell and corner slabs
       fence_proxy_async_smem();
-      issue_key(evn, d_next, p_next, sdir, slab, bar, true);
+      issue_key(evn, d_next, p_next, sdir, slab, bar, true, prm.err, prm.test_wait ? 16u : 0u);
     }
     pending = next_key && slab_staged(evn, p_next);
 
@@ -1095,7 +1139,9 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
     // envelope, N floats each) and written by two bulk copies; with SPLIT == 2 the |Y|^2
     // exchange uses the first 16M bytes (where E was).
     const size_t pair = static_cast<size_t>(d) * S + s;
-    const bool traces = ev.efield != nullptr;
+    // (debug build) the pair lies in the event's outputs; otherwise none of its outputs is written
+    const bool pair_ok = in_bounds(e < n_events && d >= 0 && d < ev.n_dir && s >= 0 && s < S, prm.err);
+    const bool traces = ev.efield != nullptr && pair_ok;
     const bool want_snr = kSnr && ev.snr != nullptr;
     const bool stage_env = traces || ev.peak_fine != nullptr || want_snr;   // read back by those
     float* stage = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(A) + 16 * M);
@@ -1208,7 +1254,7 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
       if (pv < 0.f) { pv = 0.f; pk = 0; }
       snr = pair_snr<T>(stage + 2 * N, N, pk, pv, redw);
     }
-    if (tid == 0) {
+    if (tid == 0 && pair_ok) {
 #pragma unroll
       for (int w = 1; w < T / 32; ++w) {
         if (redv[w] > bv || (redv[w] == bv && redi[w] < bi)) { bv = redv[w]; bi = redi[w]; }
@@ -1222,10 +1268,13 @@ __global__ void __launch_bounds__(Layout<N_>::T, Layout<N_>::MIN_CTAS) unfold_ke
                                                ev.dt_ns));
       ev.status[pair] = di.st | (key_sing ? kStSingular : 0u);
       if (want_snr) ev.snr[pair] = snr;
-      if (dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
-        // one acquire-release add: it releases this thread's outputs of the direction (the
-        // only ones the residual reads) and acquires every other CTA's; the barrier below
-        // passes them on to the CTA's other threads
+    }
+    if (tid == 0 && dir_end) {   // publish this CTA's pairs of direction d; the last CTA does the residual
+      // one acquire-release add: it releases this thread's outputs of the direction (the
+      // only ones the residual reads) and acquires every other CTA's; the barrier below
+      // passes them on to the CTA's other threads
+      *sflag = 0;
+      if (pair_ok) {
         const unsigned before = atom_add_acq_rel(ev.dir_done + d, static_cast<unsigned>(pairs_in_dir));
         *sflag = (before + pairs_in_dir == static_cast<unsigned>(S)) ? 1 : 0;
       }

@@ -24,3 +24,18 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def output_guard_bands(request, monkeypatch):
+    """GPU tests: every output from binding.alloc_outputs sits between guard bands, checked
+    after the test (tests/guard_util.py)."""
+    if "gpu" not in request.keywords:
+        yield
+        return
+    from guard_util import GuardRegistry, guarded_alloc_outputs
+    from paper_1507_07733_gb300 import binding
+    reg = GuardRegistry()
+    monkeypatch.setattr(binding, "alloc_outputs", guarded_alloc_outputs(reg, binding.outputs_struct))
+    yield reg
+    reg.check()

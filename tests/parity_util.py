@@ -2,8 +2,9 @@
 
 Tolerances (stated once, used everywhere):
 - E-field and envelope: relative L2 error per (station, direction) pair <= 1e-5;
-- peak index: equal, or the oracle's envelope at the GPU's index within 1e-6 relative of
-  the oracle's maximum (a tie at FP32 resolution);
+- peak index: equal, or a neighbour of the oracle's index (|diff| == 1) whose oracle
+  envelope lies within 1e-6 relative of the oracle's maximum (two samples that tie at FP32
+  resolution);
 - peak amplitude: relative error <= 1e-5;
 - peak time, residual, t0: |diff| <= 1e-9 * max(|oracle|, 1 ns); chi2: relative 1e-9 with
   a 1 ns^2 floor. Where a peak index legitimately differs, the residual of that direction
@@ -27,6 +28,14 @@ def rel_l2(a, b, axis_len):
     return np.linalg.norm(a - b, axis=1) / np.where(nb > 0, nb, 1.0)
 
 
+def is_tie(env, gi, oi):
+    """A peak index other than the oracle's is accepted only as its neighbour, with the oracle's
+    envelope at the two samples equal within TIE relative to the maximum."""
+    env = np.asarray(env, np.float64)
+    top = env[oi]
+    return abs(int(gi) - int(oi)) == 1 and abs(env[gi] - top) <= TIE * top
+
+
 def near_threshold(ref):
     return np.asarray(ref["min_margin"]) <= 1e-5
 
@@ -45,8 +54,7 @@ def check_pairs(gpu, ref, n_samples, efield=True):
     diff = np.flatnonzero(gi != oi)
     for q in diff:
         assert env is not None, f"peak index differs at pair {q} and no envelope to judge a tie"
-        top = env[q, oi[q]]
-        assert abs(env[q, gi[q]] - top) <= TIE * top, f"pair {q}: gpu idx {gi[q]} vs oracle {oi[q]} is not a tie"
+        assert is_tie(env[q], gi[q], oi[q]), f"pair {q}: gpu idx {gi[q]} vs oracle {oi[q]} is not an adjacent tie"
     pa = np.asarray(gpu["peak_amp"], np.float64).reshape(-1)
     ra = np.asarray(ref["peak_amp"]).reshape(-1)
     assert np.all(abs(pa - ra) <= REL_L2 * np.maximum(ra, 1e-30) + 1e-30), "peak amplitude"

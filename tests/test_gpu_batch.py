@@ -89,7 +89,8 @@ def test_batch_limits_refused(setup):
 
 
 def test_uneven_stream_full_size_sampled_against_oracle():
-    """The 256-event uneven workload (S 3-124, N 1024/2048/4096, D 16-256), autotuned plan."""
+    """The 256-event uneven workload (S 3-124, N 1024/2048/4096, D 16-256), autotuned plan;
+    about 2,000 of its 2.2 M pairs against the oracle, spread over the three lengths."""
     from paper_1507_07733_gb300 import binding
     ctx = binding.Context(0, autotune=True)
     pat = synth.make_pattern()
@@ -104,21 +105,29 @@ def test_uneven_stream_full_size_sampled_against_oracle():
     binding.ar_sync(ctx.h)
     ctas, ms = plan.tuning()
     assert all(c >= 1 for c in ctas) and min(m for m in ms if m > 0) > 0
+    # about 2,000 pairs against the oracle, a third per trace length, over 16 events per length
     rng = np.random.default_rng(256)
-    for ei in rng.choice(len(evs), 6, replace=False):
-        e, o = evs[ei], outs[ei]
-        q = rng.choice(e.n_stations * e.n_dirs, 3, replace=False)
-        di, si = q // e.n_stations, q % e.n_stations
-        ref = oracle.unfold_sample(pat, e, si, di)
-        sub = {k: o[k].cpu().numpy()[di, si] for k in ("efield", "envelope", "peak_idx", "peak_amp", "status")}
-        check_pairs(sub, ref, e.n_samples)
-        check_times(o["peak_time_ns"].cpu().numpy()[di, si], ref["peak_time_ns"], "peak time")
-        # every direction's residual from the batch's own peak times
-        pt = o["peak_time_ns"].cpu().numpy()
-        res = o["residual_ns"].cpu().numpy()
-        for d in rng.choice(e.n_dirs, 2, replace=False):
-            r, t0, chi2 = oracle.residual(e.pos_m, pt[d], *e.dirs_rad[d])
-            check_times(res[d], r, "residual")
+    checked = 0
+    for n in (1024, 2048, 4096):
+        cls = [i for i, e in enumerate(evs) if e.n_samples == n]
+        pick = rng.choice(cls, min(16, len(cls)), replace=False)
+        for ei in pick:
+            e, o = evs[ei], outs[ei]
+            k = min(e.n_stations * e.n_dirs, -(-667 // len(pick)))
+            q = rng.choice(e.n_stations * e.n_dirs, k, replace=False)
+            di, si = q // e.n_stations, q % e.n_stations
+            ref = oracle.unfold_sample(pat, e, si, di)
+            sub = {kk: o[kk].cpu().numpy()[di, si] for kk in ("efield", "envelope", "peak_idx", "peak_amp", "status")}
+            check_pairs(sub, ref, e.n_samples)
+            check_times(o["peak_time_ns"].cpu().numpy()[di, si], ref["peak_time_ns"], "peak time")
+            checked += k
+            # two directions' residuals from the batch's own peak times
+            pt = o["peak_time_ns"].cpu().numpy()
+            res = o["residual_ns"].cpu().numpy()
+            for d in rng.choice(e.n_dirs, 2, replace=False):
+                r, t0, chi2 = oracle.residual(e.pos_m, pt[d], *e.dirs_rad[d])
+                check_times(res[d], r, "residual")
+    assert checked >= 1900
     plan.close()
     del outs, inputs
     torch.cuda.empty_cache()

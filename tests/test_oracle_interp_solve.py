@@ -157,3 +157,21 @@ def test_solve_singular_rule():
         assert s == expect, eps
         if not s:
             assert np.max(abs(H @ E - V)) <= 1e-6
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_solve_and_singular_rule_are_scale_invariant(scale):
+    """H scaled by s gives E / s and the same singular decisions: the rule compares |det| with
+    a product of two magnitudes, both quadratic in s. Powers of ten are not exact in binary,
+    so E is compared to FP64 rounding."""
+    rng = np.random.default_rng(12)
+    V = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+    for _ in range(100):
+        H = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        E, s, m = oracle.solve(H, V)
+        Es, ss, ms = oracle.solve(H * scale, V)
+        assert ss == s and abs(ms - m) <= 1e-12 * max(m, 1e-300)
+        assert np.max(abs(Es * scale - E)) <= 1e-12 * np.linalg.cond(H) * np.max(abs(E))
+    for eps, expect in ((1e-7, 1), (1.9e-6, 1), (2.1e-6, 0)):
+        H = np.array([[1.0, 1.0], [1.0, 1.0 + eps]], complex) * scale
+        assert oracle.solve(H, V)[1] == expect, (scale, eps)
