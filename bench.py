@@ -198,6 +198,26 @@ def time_oracle(pat, ev, steps: int, warmup: int):
     return pairs, dt, threads
 
 
+def time_oracle_configs(pat):
+    """The oracle over whole workloads: the single event (10 x 2048, 1 direction), the same at
+    4096 samples, and the whole direction scan (124 x 2048 x 64 directions, 7,936 pairs), each
+    once, on all host cores."""
+    import oracle
+    from paper_1507_07733_gb300 import synth
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count() or 1
+    oracle.set_threads(threads)
+    out = {}
+    for name, ev in (("single_event_10x2048x1", synth.single_event(2048)),
+                     ("single_event_10x4096x1", synth.single_event(4096)),
+                     ("direction_scan_124x2048x64", synth.direction_scan())):
+        t = time.perf_counter()
+        oracle.unfold_event(pat, ev)
+        el = time.perf_counter() - t
+        pairs = ev.n_stations * ev.n_dirs
+        out[name] = {"pairs": pairs, "seconds": round(el, 3), "unfolds_per_s": round(pairs / el, 2), "cores": threads}
+    return out
+
+
 # ---- the GPU arm -----------------------------------------------------------------------
 
 def run_gpu(args):
@@ -332,10 +352,14 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        p_pairs, p_dt, threads = time_oracle(pat, ev, steps=args.cpu_steps, warmup=1)
-        cpu = {"value": round(p_pairs / p_dt, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{args.cpu_steps} x (1 station x 16 directions) of the workload, FP64 oracle "
-                         f"(naive DFTs), OpenMP over pairs; {p_pairs} pairs in {p_dt:.2f} s"}
+        # the oracle over whole workloads; the whole scan (about 16 s of CPU work on 16 cores)
+        # is the baseline
+        oc = time_oracle_configs(pat)
+        scan = oc["direction_scan_124x2048x64"]
+        cpu = {"value": scan["unfolds_per_s"], "unit": UNIT, "cores": scan["cores"], "kind": "oracle",
+               "sample": f"the whole workload once: {scan['pairs']} pairs in {scan['seconds']} s, FP64 oracle "
+                         f"(naive DFTs), OpenMP over pairs",
+               "configs": oc}
 
     ctx.close()
     if rank == 0:
@@ -796,6 +820,7 @@ def run_batched(args, binding, synth, ctx, pid, dev, stream):
     torch.cuda.synchronize(dev)
     batch_ms = timed(lambda: plan.run(bstructs, ostructs), reps)
     ctas, tune_ms = plan.tuning()
+    plan_info = plan.tuning_info()
     binding.ar_sync(ctx.h, sp)
     binding.ar_sync(bctx.h, sp)
     plan.close()
@@ -808,15 +833,20 @@ def run_batched(args, binding, synth, ctx, pid, dev, stream):
             "plain_ms": round(plain_ms, 3), "plain_unfolds_per_s": round(pairs / plain_ms * 1e3, 1),
             "batched_ms": round(batch_ms, 3), "batched_unfolds_per_s": round(pairs / batch_ms * 1e3, 1),
             "speedup": round(plain_ms / batch_ms, 3), "batched_GBps": round(out_bytes / batch_ms / 1e6, 1),
-            "ctas_per_sm": list(ctas), "autotune_graph_ms": [round(x, 3) for x in tune_ms]}
+            "ctas_per_sm": list(ctas), "autotune_graph_ms": [round(x, 3) for x in tune_ms],
+            "plan_per_class": {"classes": ["1024", "2048", "4096"], **plan_info}}
 
 
 def run_serving(args, binding, synth, dev):
-    """Poisson event streams at several rates with the uneven size distribution, served by
-    the continuous-batching server vs the plain one (one event per launch, one in flight).
-    Requests carry host (pinned) buffers; outputs are the peaks, residuals, t0 and chi2 (the
-    E-field traces stay on the device side). Latency runs from the scheduled arrival to the
-    server's completion stamp (same monotonic clock)."""
+    """The continuous-batching server against the plain one (one event per launch, one in
+    flight) on streams of the uneven size distribution, in two output modes:
+      peaks  peaks, residuals, t0, chi2 and status returned to pinned host buffers;
+      full   the E-field and envelope traces as well (on average about 240 MB per event, so
+             the device-to-host link, about 190 GB/s, bounds throughput near 800 events/s).
+    Per mode: Poisson arrivals at offered rates, each run for min(5 s of arrivals, 5,000
+    events) -- so at least 5 s or 5,000 events -- and a closed loop that keeps `depth` requests
+    outstanding for 5 s, which measures each server's ceiling. Latency runs from the scheduled
+    arrival (closed loop: the submit stamp) to the server's completion stamp, same clock."""
     import torch
     ctx = binding.Context(dev.index if dev.index is not None else 0)
     pid = ctx.load_pattern(synth.make_pattern())
@@ -824,67 +854,139 @@ def run_serving(args, binding, synth, dev):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     keep = [tuple(pin(a) for a in (e.traces, e.pos_m, e.t_start_ns, e.dirs_rad)) for e in pool]
     evs = [binding.make_event(pid, *k, e.fs_hz) for k, e in zip(keep, pool)]
-    R = 256
+    pairs_of = [e.n_stations * e.n_dirs for e in pool]
     smax, dmax = 124, 256
-    slots = []
-    for _ in range(R):
-        o = {"efield": None, "envelope": None,
-             "peak_idx": torch.empty(dmax * smax, dtype=torch.int32).pin_memory(),
-             "peak_amp": torch.empty(dmax * smax, dtype=torch.float32).pin_memory(),
-             "peak_time_ns": torch.empty(dmax * smax, dtype=torch.float64).pin_memory(),
-             "residual_ns": torch.empty(dmax * smax, dtype=torch.float64).pin_memory(),
-             "t0_ns": torch.empty(dmax, dtype=torch.float64).pin_memory(),
-             "chi2": torch.empty(dmax, dtype=torch.float64).pin_memory(),
-             "status": torch.empty(dmax * smax, dtype=torch.int32).pin_memory()}
-        slots.append(binding.outputs_struct(o))
-        slots[-1]._t = o
-    rates = [200, 500, 1000, 2000, 5000]
-    seconds = 1.0
-    result = {"mode": "peaks, residuals, t0, chi2 returned to pinned host buffers (traces host->device)",
-              "event_pool": "64 events of the uneven distribution (S U{3..124}, N {1024,2048,4096}, D U{16..256})",
-              "state_budget_bytes": 4 << 30, "rates": {}}
-    for kind, cfg in (("batched", dict(max_batch_events=32, max_inflight=2)),
-                      ("plain", dict(max_batch_events=1, max_inflight=1))):
-        srv = binding.Server(ctx, state_budget_bytes=4 << 30, max_stations_per_event=124, max_n_freq=51, **cfg)
-        # warm-up: every pool event once (tables, graph, autotune-free plan)
-        warm = [srv.submit(evs[i], slots[i % R]) for i in range(len(evs))]
-        for t in warm:
-            srv.wait(t)
-            srv.release(t)
-        for lam in rates:
-            n = int(lam * seconds)
-            arr = synth.poisson_arrivals(lam, n, seed_key=lam)
+
+    def peak_slots(R):
+        slots = []
+        for _ in range(R):
+            o = {"efield": None, "envelope": None,
+                 "peak_idx": torch.empty(dmax * smax, dtype=torch.int32).pin_memory(),
+                 "peak_amp": torch.empty(dmax * smax, dtype=torch.float32).pin_memory(),
+                 "peak_time_ns": torch.empty(dmax * smax, dtype=torch.float64).pin_memory(),
+                 "residual_ns": torch.empty(dmax * smax, dtype=torch.float64).pin_memory(),
+                 "t0_ns": torch.empty(dmax, dtype=torch.float64).pin_memory(),
+                 "chi2": torch.empty(dmax, dtype=torch.float64).pin_memory(),
+                 "status": torch.empty(dmax * smax, dtype=torch.int32).pin_memory()}
+            s = binding.outputs_struct(o)
+            s._t = o
+            slots.append(s)
+        return slots
+
+    # full outputs: one pinned output set per pool event (the events up to ~12 GB of outputs)
+    full_n = 0
+    full_bytes = 0
+    for e in pool:
+        b = e.n_dirs * e.n_stations * (12 * e.n_samples + 40)
+        if full_bytes + b > (12 << 30):
+            break
+        full_bytes += b
+        full_n += 1
+    result = {"event_pool": "64 events of the uneven distribution (S U{3..124}, N {1024,2048,4096}, D U{16..256})",
+              "state_budget_bytes": 4 << 30, "modes": {}}
+    modes = {
+        "peaks": dict(desc="peaks, residuals, t0, chi2, status returned to pinned host buffers",
+                      rates=[200, 1000, 5000, 20000, 50000], n_pool=len(pool)),
+        "full": dict(desc=f"E-field and envelope returned as well (the first {full_n} pool events, "
+                          f"{full_bytes / 2**30:.1f} GiB of pinned outputs, {full_bytes / max(full_n, 1) / 1e6:.0f} MB "
+                          "per event on average)",
+                     rates=[100, 300, 600], n_pool=full_n),
+    }
+    for mode, spec in modes.items():
+        n_pool = spec["n_pool"]
+        if mode == "peaks":
+            R = 256
+            slots = peak_slots(R)
+            slot_of = lambda i: i % R
+        else:
+            R = n_pool
+            slots = [binding.alloc_outputs(pool[k].n_dirs, pool[k].n_stations, pool[k].n_samples, device="cpu",
+                                           pin_memory=True)[1] for k in range(n_pool)]
+            slot_of = lambda i: i % n_pool
+        mres = {"mode": spec["desc"], "rates": {}, "closed_loop": {}}
+        for kind, cfg in (("batched", dict(max_batch_events=32, max_inflight=2)),
+                          ("plain", dict(max_batch_events=1, max_inflight=1))):
+            srv = binding.Server(ctx, state_budget_bytes=4 << 30, max_stations_per_event=124, max_n_freq=51, **cfg)
+            warm = [srv.submit(evs[i], slots[slot_of(i)]) for i in range(n_pool)]   # tables, graphs
+            for t in warm:
+                srv.wait(t)
+                srv.release(t)
+
+            def stream(n, arrival):
+                """Submit n requests (arrival(i) -> absolute target time or None), return stats."""
+                owner = [None] * R
+                tickets = []
+                pairs = 0
+                t0 = time.perf_counter()
+                for i in range(n):
+                    target = arrival(i, t0)
+                    if target is not None:
+                        while time.perf_counter() < target:
+                            pass
+                    j = slot_of(i)
+                    if owner[j] is not None:
+                        srv.wait(owner[j])
+                    k = i % n_pool
+                    tk = srv.submit(evs[k], slots[j])
+                    owner[j] = tk
+                    tickets.append((tk, target))
+                    pairs += pairs_of[k]
+                lat, last = [], 0.0
+                for tk, target in tickets:
+                    srv.wait(tk, 600000)
+                    _, sub, done = srv.times(tk)
+                    lat.append(done / 1e9 - (target if target is not None else sub / 1e9))
+                    last = max(last, done / 1e9)
+                    srv.release(tk)
+                span = last - t0
+                lat_ms = np.array(lat) * 1e3
+                return {"events": n, "seconds": round(span, 3), "throughput_events_per_s": round(n / span, 1),
+                        "unfolds_per_s": round(pairs / span, 1),
+                        "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                        "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)}
+
+            for lam in spec["rates"]:
+                n = int(min(5000, 5 * lam))
+                arr = synth.poisson_arrivals(lam, n, seed_key=lam)
+                r = stream(n, lambda i, t0: t0 + arr[i])
+                r["offered_events_per_s"] = lam
+                mres["rates"].setdefault(str(lam), {})[kind] = r
+            # closed loop: `depth` requests outstanding, for 5 s
+            depth = min(R, 64)
             owner = [None] * R
-            tickets = []
-            pairs = 0
+            done_n, pairs, lat = 0, 0, []
             t0 = time.perf_counter()
-            for i in range(n):
-                target = t0 + arr[i]
-                while time.perf_counter() < target:
-                    pass
-                j = i % R
-                if owner[j] is not None:
-                    srv.wait(owner[j])
-                k = i % len(evs)
-                tk = srv.submit(evs[k], slots[j])
-                owner[j] = tk
-                tickets.append((tk, target))
-                pairs += pool[k].n_stations * pool[k].n_dirs
-            lat = []
-            last = 0.0
-            for tk, target in tickets:
-                srv.wait(tk)
-                st, _, done = srv.times(tk)
-                lat.append(done / 1e9 - target)
-                last = max(last, done / 1e9)
+            i = 0
+            inflight = []
+            while time.perf_counter() - t0 < 5.0 or inflight:
+                if time.perf_counter() - t0 < 5.0 and len(inflight) < depth:
+                    j = slot_of(i)
+                    if owner[j] is not None and owner[j] in inflight:
+                        pass
+                    else:
+                        k = i % n_pool
+                        tk = srv.submit(evs[k], slots[j])
+                        owner[j] = tk
+                        inflight.append(tk)
+                        pairs += pairs_of[k]
+                        i += 1
+                        continue
+                tk = inflight.pop(0)
+                srv.wait(tk, 600000)
+                _, sub, done = srv.times(tk)
+                lat.append((done - sub) / 1e6)
                 srv.release(tk)
-            span = last - t0
-            lat_ms = np.array(lat) * 1e3
-            result["rates"].setdefault(str(lam), {})[kind] = {
-                "events": n, "throughput_events_per_s": round(n / span, 1),
-                "unfolds_per_s": round(pairs / span, 1), "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                done_n += 1
+            span = time.perf_counter() - t0
+            lat_ms = np.array(lat)
+            mres["closed_loop"][kind] = {
+                "depth": depth, "events": done_n, "seconds": round(span, 3),
+                "throughput_events_per_s": round(done_n / span, 1), "unfolds_per_s": round(pairs / span, 1),
+                "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
                 "p99_ms": round(float(np.percentile(lat_ms, 99)), 3)}
-        srv.close()
+            srv.close()
+        result["modes"][mode] = mres
+        del slots
     ctx.close()
     return result
 

@@ -277,9 +277,11 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* limits, ar_batch**
  * pointers as for ar_unfold) as one graph launch on stream. Asynchronous: returns once the
  * launch is queued. Two runs may be in flight; a third waits on the host for the first to
  * finish with its staging buffer. If the context was created with autotune = 1, the first
- * run times the unfold kernels at 1..4 CTAs per SM (running the batch several times; the
- * results are the same each time) and keeps the fastest. Device errors are reported by
- * ar_sync on the plan's context.
+ * run tunes the plan on its events (running the batch several times; the results are the
+ * same each time): first every length class at a common 1..6 CTAs per SM, then each class on
+ * its own, longest traces first, over its CTAs per SM and the placement of its corner slabs
+ * (staged in shared memory where they fit, or read from L2), keeping what is fastest (see
+ * ar_batch_tuning_info). Device errors are reported by ar_sync on the plan's context.
  * Errors: AR_ERR_INVALID_ARG, AR_ERR_UNSUPPORTED_N, AR_ERR_NO_PATTERN, AR_ERR_BUDGET (the
  * events exceed the plan's limits), AR_ERR_CUDA. */
 ar_status ar_batch_run(ar_batch* plan, const ar_event* events, const ar_outputs* outs, int32_t n_events,
@@ -290,6 +292,22 @@ ar_status ar_batch_run(ar_batch* plan, const ar_event* events, const ar_outputs*
  * not tried, e.g. beyond what every class can hold; may be NULL). A candidate k runs each
  * class at min(k, the most CTAs per SM it can hold). */
 ar_status ar_batch_tuning(const ar_batch* plan, int32_t* ctas_per_sm, float* candidate_ms);
+
+/* The plan per trace-length class (index 0, 1, 2 = 1024, 2048, 4096 samples), as the
+ * autotuner left it (or the defaults: the most CTAs per SM, slabs staged where that costs no
+ * occupancy). */
+typedef struct ar_batch_plan_info {
+  int32_t ctas_per_sm[3];      /* unfold CTAs per SM */
+  int32_t slabs_staged[3];     /* 1: corner slabs staged in shared memory; 0: read from L2 */
+  int32_t max_ctas_per_sm[3];  /* the most the class's unfold kernel can hold */
+  int32_t tuned;               /* 1 once the autotuner has run (autotune = 1 and a first run) */
+  int32_t candidates;          /* plans it timed */
+  float default_ms;            /* graph time of the untuned plan on the tuning run's events */
+  float tuned_ms;              /* graph time of the chosen plan on the same events */
+} ar_batch_plan_info;
+
+/* Errors: AR_ERR_INVALID_ARG (NULL). */
+ar_status ar_batch_tuning_info(const ar_batch* plan, ar_batch_plan_info* info);
 
 /* Wait for the plan's runs in flight and free it. NULL is a no-op. */
 ar_status ar_batch_destroy(ar_batch* plan);

@@ -34,7 +34,8 @@ AR_STATUS_BAD_PATTERN = 8
 EXPORTED = ["ar_create", "ar_destroy", "ar_last_error", "ar_status_string", "ar_load_pattern",
             "ar_prepare", "ar_unfold", "ar_sync", "ar_unfold_host", "ar_set_profiling", "ar_kernel_times",
             "ar_set_test_fault",
-            "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_destroy",
+            "ar_unfold_noalloc", "ar_batch_create", "ar_batch_run", "ar_batch_tuning", "ar_batch_tuning_info",
+            "ar_batch_destroy",
             "ar_server_create", "ar_submit", "ar_poll", "ar_wait", "ar_ticket_times", "ar_ticket_release",
             "ar_server_destroy", "ar_reconstruct", "ar_unfold_tc"]
 
@@ -72,6 +73,12 @@ class ar_event(ctypes.Structure):
 class ar_batch_limits(ctypes.Structure):
     _fields_ = [("max_events", ctypes.c_int32), ("max_stations", ctypes.c_int32), ("max_dirs", ctypes.c_int32),
                 ("max_n_freq", ctypes.c_int32)]
+
+
+class ar_batch_plan_info(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32 * 3), ("slabs_staged", ctypes.c_int32 * 3),
+                ("max_ctas_per_sm", ctypes.c_int32 * 3), ("tuned", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("default_ms", ctypes.c_float), ("tuned_ms", ctypes.c_float)]
 
 
 class ar_outputs(ctypes.Structure):
@@ -126,6 +133,7 @@ def load(path: str | None = None):
         L.ar_batch_create.argtypes = [vp, ctypes.POINTER(ar_batch_limits), ctypes.POINTER(vp)]
         L.ar_batch_run.argtypes = [vp, vp, vp, i32, vp]
         L.ar_batch_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+        L.ar_batch_tuning_info.argtypes = [vp, ctypes.POINTER(ar_batch_plan_info)]
         L.ar_batch_destroy.argtypes = [vp]
         u64, i64 = ctypes.c_uint64, ctypes.c_int64
         L.ar_server_create.argtypes = [vp, ctypes.POINTER(ar_server_config), ctypes.POINTER(vp)]
@@ -251,6 +259,15 @@ def ar_batch_tuning(plan):
     if st != AR_OK:
         raise ArError(st, "ar_batch_tuning")
     return tuple(c), tuple(ms)
+
+
+def ar_batch_tuning_info(h) -> dict:
+    """The plan per length class (1024, 2048, 4096 samples) and the autotuner's timings."""
+    i = ar_batch_plan_info()
+    _check(None, load().ar_batch_tuning_info(h, ctypes.byref(i)))
+    return {"ctas_per_sm": list(i.ctas_per_sm), "slabs_staged": list(i.slabs_staged),
+            "max_ctas_per_sm": list(i.max_ctas_per_sm), "tuned": bool(i.tuned), "candidates": i.candidates,
+            "default_ms": round(i.default_ms, 4), "tuned_ms": round(i.tuned_ms, 4)}
 
 
 def ar_batch_destroy(plan) -> None:
@@ -475,6 +492,10 @@ class Batch:
 
     def tuning(self):
         return ar_batch_tuning(self.h)
+
+    def tuning_info(self) -> dict:
+        """The plan per length class (1024, 2048, 4096 samples) and the autotuner's timings."""
+        return ar_batch_tuning_info(self.h)
 
     def close(self):
         if self.h:

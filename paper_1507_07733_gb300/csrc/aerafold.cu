@@ -1222,8 +1222,12 @@ struct ar_batch {
   int ctas_per_sm[kClasses] = {0, 0, 0};       // chosen unfold occupancy per class
   int max_ctas_per_sm[kClasses] = {0, 0, 0};
   int slab_direct[kClasses] = {0, 0, 0};       // corner slabs read from L2 where staging them costs occupancy
+  int max_staged[kClasses] = {0, 0, 0};        // the most CTAs per SM with the slabs staged (0: they do not fit)
+  int max_direct[kClasses] = {0, 0, 0};        // ... with the slabs read from L2
   bool tuned = false;
-  float tune_ms[kTuneMax + 1] = {};            // graph time per candidate CTAs per SM (autotune)
+  float tune_ms[kTuneMax + 1] = {};            // graph time per candidate CTAs per SM (autotune, stage 1)
+  float default_ms = 0.f, tuned_ms = 0.f;      // graph time of the untuned and of the chosen plan
+  int candidates = 0;                          // plans the autotuner timed
 };
 
 namespace {
@@ -1396,6 +1400,8 @@ ar_status ar_batch_create(ar_ctx* ctx, const ar_batch_limits* lim, ar_batch** ou
     int per_sm_direct = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_direct, fn, threads, smem_of(true))) != cudaSuccess)
       return cleanup(fail(ctx, AR_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e)));
+    b->max_staged[c] = b->max_ctas_per_sm[c];
+    b->max_direct[c] = per_sm_direct;
     if (per_sm_direct > b->max_ctas_per_sm[c]) {
       b->slab_direct[c] = 1;
       b->max_ctas_per_sm[c] = per_sm_direct;
@@ -1432,42 +1438,93 @@ ar_status ar_batch_destroy(ar_batch* b) {
   return AR_OK;
 }
 
-// Autotune: time the whole graph for each unfold occupancy 1..max CTAs per SM (clamped per
-// class) on the current staging set, keep the fastest, rebuild both graphs with it.
+// Time the whole graph of staging set `set` with the given CTAs per SM per class (the classes'
+// slab staging as b->slab_direct holds it): one untimed launch, then the mean of three.
+static ar_status batch_time_plan(ar_batch* b, int set, const int* ctas, bool snr, cudaStream_t stream,
+                                 cudaEvent_t t0, cudaEvent_t t1, float* ms_out) {
+  ar_ctx* ctx = b->ctx;
+  cudaGraphExec_t g = nullptr;
+  ar_status st = batch_build_graph(b, set, ctas, snr, &g);
+  if (st != AR_OK) return st;
+  float ms_sum = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {
+    AR_CUDA(ctx, cudaEventRecord(t0, stream));
+    AR_CUDA(ctx, cudaGraphLaunch(g, stream));
+    AR_CUDA(ctx, cudaEventRecord(t1, stream));
+    AR_CUDA(ctx, cudaEventSynchronize(t1));
+    float ms = 0.f;
+    AR_CUDA(ctx, cudaEventElapsedTime(&ms, t0, t1));
+    if (rep > 0) ms_sum += ms;
+  }
+  cudaGraphExecDestroy(g);
+  ++b->candidates;
+  *ms_out = ms_sum / 3.f;
+  return AR_OK;
+}
+
+// Stage the corner slabs of class c in shared memory (direct = 0) or read them from L2 (1), in
+// the plan and in the descriptors of staging set `set`.
+static void batch_set_slabs(ar_batch* b, int set, int c, int direct) {
+  b->slab_direct[c] = direct;
+  BatchHeader* hdr = reinterpret_cast<BatchHeader*>(b->h_stage[set][c]);
+  EventDesc* d = const_cast<EventDesc*>(batch_events(hdr));
+  for (int i = 0; i < hdr->n_events; ++i) d[i].slab_direct = direct;
+}
+
+// Autotune, on the events of staging set `set` (their results are the same for every plan).
+// Stage 1: every class at min(k, its most CTAs per SM) for k = 1..6, keep the fastest k.
+// Stage 2: per class, longest traces first, the CTAs per SM (1..its most) and the corner-slab
+// placement (staged in shared memory where it fits, or read from L2) with the other classes
+// fixed at their current choice; keep what is fastest. Classes without events keep stage 1's.
+// Then both graphs are rebuilt with the plan.
 static ar_status batch_autotune(ar_batch* b, int set, bool snr, cudaStream_t stream) {
   ar_ctx* ctx = b->ctx;
-  int best_k = 0;
-  float best_ms = 0.f;
   cudaEvent_t t0, t1;
   AR_CUDA(ctx, cudaEventCreate(&t0));
   AR_CUDA(ctx, cudaEventCreate(&t1));
+  b->candidates = 0;
+  ar_status st = batch_time_plan(b, set, b->ctas_per_sm, snr, stream, t0, t1, &b->default_ms);
+  int best[kClasses];
+  float best_ms = b->default_ms;
+  for (int c = 0; c < kClasses; ++c) best[c] = b->ctas_per_sm[c];
   const int kmax = std::max(b->max_ctas_per_sm[0], std::max(b->max_ctas_per_sm[1], b->max_ctas_per_sm[2]));
-  for (int k = 1; k <= kmax && k <= kTuneMax; ++k) {
+  for (int k = 1; st == AR_OK && k <= kmax && k <= kTuneMax; ++k) {
     int ctas[kClasses];
     for (int c = 0; c < kClasses; ++c) ctas[c] = std::min(k, b->max_ctas_per_sm[c]);
-    cudaGraphExec_t g = nullptr;
-    ar_status st = batch_build_graph(b, set, ctas, snr, &g);
-    if (st != AR_OK) return st;
-    float ms_sum = 0.f;
-    for (int rep = 0; rep < 4; ++rep) {
-      AR_CUDA(ctx, cudaEventRecord(t0, stream));
-      AR_CUDA(ctx, cudaGraphLaunch(g, stream));
-      AR_CUDA(ctx, cudaEventRecord(t1, stream));
-      AR_CUDA(ctx, cudaEventSynchronize(t1));
-      float ms = 0.f;
-      AR_CUDA(ctx, cudaEventElapsedTime(&ms, t0, t1));
-      if (rep > 0) ms_sum += ms;
-    }
-    cudaGraphExecDestroy(g);
-    b->tune_ms[k] = ms_sum / 3.f;
-    if (best_k == 0 || b->tune_ms[k] < best_ms) {
-      best_k = k;
+    st = batch_time_plan(b, set, ctas, snr, stream, t0, t1, &b->tune_ms[k]);
+    if (st == AR_OK && b->tune_ms[k] < best_ms) {
       best_ms = b->tune_ms[k];
+      for (int c = 0; c < kClasses; ++c) best[c] = ctas[c];
     }
+  }
+  for (int c = 2; st == AR_OK && c >= 0; --c) {
+    if (reinterpret_cast<const BatchHeader*>(b->h_stage[set][c])->total_pairs == 0) continue;
+    const int direct0 = b->slab_direct[c];
+    int best_direct = direct0;
+    for (int direct = 0; st == AR_OK && direct <= 1; ++direct) {
+      const int most = direct ? b->max_direct[c] : b->max_staged[c];
+      if (most < 1) continue;
+      batch_set_slabs(b, set, c, direct);
+      for (int k = 1; st == AR_OK && k <= most && k <= kTuneMax; ++k) {
+        if (k == best[c] && direct == direct0) continue;   // timed already
+        int ctas[kClasses] = {best[0], best[1], best[2]};
+        ctas[c] = k;
+        float ms = 0.f;
+        st = batch_time_plan(b, set, ctas, snr, stream, t0, t1, &ms);
+        if (st == AR_OK && ms < best_ms) {
+          best_ms = ms;
+          best[c] = k;
+          best_direct = direct;
+        }
+      }
+    }
+    batch_set_slabs(b, set, c, best_direct);
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  for (int c = 0; c < kClasses; ++c) b->ctas_per_sm[c] = std::min(best_k, b->max_ctas_per_sm[c]);
+  if (st != AR_OK) return st;
+  b->tuned_ms = best_ms;
+  for (int c = 0; c < kClasses; ++c) b->ctas_per_sm[c] = best[c];
   for (int s2 = 0; s2 < 2; ++s2) {
     if (b->pending[s2]) AR_CUDA(ctx, cudaEventSynchronize(b->done[s2]));
     b->pending[s2] = false;
@@ -1475,8 +1532,8 @@ static ar_status batch_autotune(ar_batch* b, int set, bool snr, cudaStream_t str
       if (b->exec[s2][v]) cudaGraphExecDestroy(b->exec[s2][v]);
       b->exec[s2][v] = nullptr;
     }
-    ar_status st = batch_build_graph(b, s2, b->ctas_per_sm, snr, &b->exec[s2][snr ? 1 : 0]);
-    if (st != AR_OK) return st;
+    ar_status st2 = batch_build_graph(b, s2, b->ctas_per_sm, snr, &b->exec[s2][snr ? 1 : 0]);
+    if (st2 != AR_OK) return st2;
   }
   b->tuned = true;
   return AR_OK;
@@ -1516,6 +1573,20 @@ ar_status ar_batch_tuning(const ar_batch* b, int32_t* ctas_per_sm, float* candid
   for (int c = 0; c < kClasses; ++c) ctas_per_sm[c] = b->ctas_per_sm[c];
   if (candidate_ms)
     for (int k = 0; k < kTuneMax; ++k) candidate_ms[k] = b->tune_ms[k + 1];
+  return AR_OK;
+}
+
+ar_status ar_batch_tuning_info(const ar_batch* b, ar_batch_plan_info* info) {
+  if (!b || !info) return AR_ERR_INVALID_ARG;
+  for (int c = 0; c < kClasses; ++c) {
+    info->ctas_per_sm[c] = b->ctas_per_sm[c];
+    info->slabs_staged[c] = b->slab_direct[c] ? 0 : 1;
+    info->max_ctas_per_sm[c] = b->max_ctas_per_sm[c];
+  }
+  info->tuned = b->tuned && b->ctx->cfg.autotune ? 1 : 0;
+  info->candidates = b->candidates;
+  info->default_ms = b->default_ms;
+  info->tuned_ms = b->tuned_ms;
   return AR_OK;
 }
 

@@ -105,6 +105,10 @@ def test_uneven_stream_full_size_sampled_against_oracle():
     binding.ar_sync(ctx.h)
     ctas, ms = plan.tuning()
     assert all(c >= 1 for c in ctas) and min(m for m in ms if m > 0) > 0
+    info = plan.tuning_info()   # the per-class plan: within each class's limits, no slower than the default
+    assert info["tuned"] and info["candidates"] >= 6 and info["ctas_per_sm"] == list(ctas)
+    assert all(1 <= c <= m for c, m in zip(info["ctas_per_sm"], info["max_ctas_per_sm"]))
+    assert 0 < info["tuned_ms"] <= info["default_ms"]
     # about 2,000 pairs against the oracle, a third per trace length, over 16 events per length
     rng = np.random.default_rng(256)
     checked = 0

@@ -13,7 +13,7 @@ def header_fields(name):
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = []
     for decl in body.split(";"):
-        decl = decl.strip()
+        decl = re.sub(r"\[\w*\]", "", decl).strip()   # array fields: the name before [n]
         if not decl:
             continue
         # "int32_t n_zen;  double zen0_rad" style lines hold one declaration each after the split
@@ -24,7 +24,7 @@ def header_fields(name):
 def test_structs_match_the_header():
     from paper_1507_07733_gb300 import binding
     for name in ("ar_config", "ar_pattern_desc", "ar_event", "ar_outputs", "ar_batch_limits", "ar_recon_out",
-                 "ar_server_config"):
+                 "ar_server_config", "ar_batch_plan_info"):
         cls = getattr(binding, name)
         assert [f[0] for f in cls._fields_] == header_fields(name), name
 
