@@ -166,6 +166,12 @@ def unfold_bytes_per_launch(S: int, D: int, N: int, n_f: int) -> int:
     return S * D * (12 * N + 28) + S * ((N // 4) * 16 + 32) + D * (4 * n_f * 32 + 32)
 
 
+def unfold_l2_bytes_per_launch(S: int, D: int, N: int, n_f: int) -> int:
+    """Bytes the fused unfold kernel moves through L2: its DRAM bytes, plus the station
+    spectrum (N/4 bins x 16 B) read again for every pair (it stays in L2 after the first)."""
+    return unfold_bytes_per_launch(S, D, N, n_f) + S * (D - 1) * (N // 4) * 16
+
+
 def unfold_flops_per_pair(N: int, D: int) -> float:
     """benchFFT convention: two complex N-point inverse transforms (5 N log2 N each), ~16 N for
     solve, envelope and peak, plus the station's forward transform amortised over D."""
@@ -287,6 +293,7 @@ def run_gpu(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     nbytes = unfold_bytes_per_launch(S, D, N, pat.n_freq)
+    l2_bytes = unfold_l2_bytes_per_launch(S, D, N, pat.n_freq)
     achieved = nbytes / (k3 / 1e3) / 1e9
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
@@ -373,7 +380,15 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 3), "traffic": traffic, "peak_source": peak_src,
                          "kernel": "unfold_kernel<2048>", "kernel_ms": round(k3, 5),
-                         "algorithmic_bytes_per_launch": nbytes},
+                         "algorithmic_bytes_per_launch": nbytes,
+                         "note": "about 63 MB of each launch's 196.7 MB of outputs are still dirty in L2 when "
+                                 "the kernel ends (ncu: 134 MB written to DRAM inside the launch) and are "
+                                 "written back during the untimed L2 flush between steps; back-to-back calls "
+                                 "without the flush are in back_to_back"},
+            "roofline_l2": {"bound": "l2", "achieved": round(l2_bytes / (k3 / 1e3) / 1e9, 1), "peak": l2_gbs,
+                            "unit": "GB/s", "frac": round(l2_bytes / (k3 / 1e3) / 1e9 / l2_gbs, 3) if l2_gbs else None,
+                            "algorithmic_bytes_per_launch": l2_bytes,
+                            "peak_source": "bench's own L2-resident copy rate (a lower bound on L2 bandwidth)"},
             "roofline_alu": alu,
             "kernel_ms": {"station_spectrum": round(k1, 5), "unfold_with_residual": round(k3, 5)},
             "gpu_launches": 2 * args.steps,

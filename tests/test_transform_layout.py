@@ -9,9 +9,14 @@ T1[r][mb][ja] = exp(2 pi i (k_lo + ja)(r + 4 mb) / N) is applied:
   * 1024 and 4096 samples: in pass 1, after its DFT;
   * 2048 samples: in pass 2, as c u^i per row i, with the rows past k_lo mod P shifted by
     one input slot in pass 1 (slot 0 turned by i^r).
-This test restates both in numpy, in FP64, and checks them against the direct sum for band
-offsets with every kind of k_lo mod P, so that the index arithmetic is pinned on the CPU.
-It shares nothing with the oracle or the CUDA path.
+This test restates both factorisations in numpy, in FP64, and checks them against the direct
+sum for band offsets with every kind of k_lo mod P: it pins the mathematics the kernels
+follow, not the kernels themselves (it runs no CUDA code and shares nothing with the oracle
+or the CUDA path). The kernels' own index arithmetic for each k_lo mod P is pinned on the GPU
+by tests/test_gpu_parity.py::test_parity_band_offsets (sampling rates that put k_lo at every
+kind of residue, at each length, against the oracle), and on the tensor-core path and the
+allocation-free entry point by the band-offset cases in tests/test_gpu_tc.py and
+tests/test_zz_no_alloc.py.
 """
 import numpy as np
 import pytest
